@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""SpMV GB/s and fraction of the HBM roofline on the 1M-row power-law matrix,
+permuted (rows and columns randomly permuted, arXiv 2308.00106 Eq. 1) vs plain.
+
+One step = one product y' = A' x' on the resident permuted matrix with the
+vectors kept in the permuted space (the iterative reuse the paper targets).
+The permutation preprocessing (keys, sort, permute_csr, entropy) runs once
+before the timed region and is reported separately.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl maxe|reference]
+                    [--workload powerlaw|laplacian|blockdiag]
+
+Multi-GPU (torchrun, one rank per GPU): the path does not shard, each rank runs
+an independent replica ("replicas only"), value = bytes of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV GB/s & frac of HBM roofline, permuted vs plain; served p50/p99 latency"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def alg_bytes(M, N, Z, vbytes, xbytes, ybytes, k=1):
+    """Algorithmic bytes of one CSR product: every byte counted once."""
+    return Z * (vbytes + 4) + (M + 1) * 4 + M * k * ybytes + N * k * xbytes
+
+
+def traffic_from_profile(name):
+    """dram bytes per launch from a committed ncu summary (line 'traffic_bytes_per_launch: N')."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None, None
+    t, kernel_rev = None, None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            t = float(line.split(":", 1)[1])
+        if line.startswith("kernel_revision:"):
+            kernel_rev = line.split(":", 1)[1].strip()
+    return t, kernel_rev
+
+
+KERNEL_REVISION = "spmm_chunk_kernel r1"  # bump whenever the SpMV kernel changes
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        for line in open(self.file.name):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        mx = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[0] >= 0.5 * mx] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2][1:5]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_workload(name, seed, device):
+    from paper_2308_00106_gb300 import workloads as W
+    if name == "powerlaw":
+        return W.powerlaw(seed, device=device), "f32", (
+            "power-law CSR 1048576x1048576, row lengths Zipf(1.5) on 1..1000, columns i+round(N(0,2000)), "
+            "FP32 values U[-1,1], int32 indices")
+    if name == "laplacian":
+        return W.laplacian5(4096, "f32", device), "f32", "5-point Laplacian on a 4096x4096 grid, FP32, natural order"
+    if name == "blockdiag":
+        return W.blockdiag(seed, device=device), "f64", (
+            "4096x4096, 16 diagonal 256x256 blocks at 2% fill + 2000 off-block entries, FP64")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def timed_steps(step, K, W, world, graph_len=50):
+    """W warm-up steps, then exactly K steps (CUDA graph replays of graph_len
+    steps plus a remainder) bracketed by barrier + synchronize; returns ms/step."""
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+    g = None
+    if graph_len > 1 and K >= graph_len:
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step()  # warm the capture stream
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(graph_len):
+                step()
+        g.replay()
+        torch.cuda.synchronize()
+    reps, rem = (K // graph_len, K % graph_len) if g is not None else (0, K)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    for _ in range(rem):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    return max_over_ranks(ms, world) / K
+
+
+def flushed_launch_ms(step, reps=20):
+    """Mean device time of one launch with L2 flushed (256 MB write) before each."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    del flush
+    return statistics.median(times)
+
+
+def cpu_baseline(A, x_np, code, seconds=10.0):
+    """The oracle's FP64 CSR product on the host (one core), bounded to ~`seconds`."""
+    import oracle
+    rp, co, va = A
+    t0 = time.perf_counter()
+    oracle.spmv(len(rp) - 1, rp, co, va, code, x_np)
+    t1 = time.perf_counter() - t0
+    reps = max(1, int(seconds / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.spmv(len(rp) - 1, rp, co, va, code, x_np)
+    return (time.perf_counter() - t0) / reps, reps
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed as it stands on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2308_00106_gb300 import workloads as W
+    oracle.build()
+    A, dtype, desc = make_workload(args.workload, args.seed, "cpu")
+    rp, co, va = A.numpy()
+    M, N, Z = A.rows, A.cols, A.nnz
+    rperm = oracle.build_permutation(args.seed, M, 0)
+    cperm = oracle.build_permutation(args.seed, N, 1)
+    prp, pco, pva = oracle.permute_csr(M, N, rp, co, va, W.DTYPE_CODE[dtype], rperm, cperm)
+    x = W.vector(1, N, "f64", "cpu").numpy()
+    code = W.DTYPE_CODE[dtype]
+    t0 = time.perf_counter()
+    oracle.spmv(M, prp, pco, pva, code, x)
+    t_full = time.perf_counter() - t0
+    budget = 150.0  # seconds for the whole run
+    frac = min(1.0, budget / max(1, args.steps + args.warmup) / max(t_full, 1e-6))
+    r1 = max(1, int(M * frac))
+    sub = (prp[:r1 + 1], pco[:prp[r1]], pva[:prp[r1]])
+    for _ in range(args.warmup):
+        oracle.spmv(r1, *sub, code, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spmv(r1, *sub, code, x)
+    dt = (time.perf_counter() - t0) / args.steps
+    vb = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
+    xb = 8 if dtype == "f64" else 4
+    z1 = int(prp[r1])
+    gbs = alg_bytes(r1, N, z1, vb, xb, xb) / dt / 1e9
+    sample = f"rows 0..{r1} of the permuted matrix ({z1} of {Z} nonzeros) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "variant": "permuted R-C, vectors in permuted space"},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["maxe", "reference"], default="maxe")
+    ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag"], default="powerlaw")
+    ap.add_argument("--seed", type=int, default=2308)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph-len", type=int, default=50)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import oracle
+    from paper_2308_00106_gb300 import maxe
+    from paper_2308_00106_gb300 import workloads as W
+
+    rank, world, local = dist_setup(args)
+    maxe.load(build_if_missing=(rank == 0))
+    A, dtype, desc = make_workload(args.workload, args.seed, "cuda")
+    M, N, Z = A.rows, A.cols, A.nnz
+    vb = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
+    xb = 8 if dtype == "f64" else 4
+    vdt = torch.float64 if dtype == "f64" else torch.float32
+
+    # ---- one-time preprocessing (Section 3: permutation; Section 4: entropy)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    rperm = maxe.maxe_build_permutation(args.seed, M, 0)
+    cperm = maxe.maxe_build_permutation(args.seed, N, 1)
+    ev[1].record()
+    hP = maxe.from_csr(A, rperm, cperm)
+    ev[2].record()
+    hN = maxe.from_csr(A)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_perm, t_pcsr = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    t0 = time.perf_counter()
+    H_perm, _ = maxe.maxe_nnz_entropy(hP, 64, 64, counts=False)
+    t_ent = (time.perf_counter() - t0) * 1e3
+    H_plain, _ = maxe.maxe_nnz_entropy(hN, 64, 64, counts=False)
+
+    x = W.vector(1, N, "f64" if dtype == "f64" else "f32", "cuda")
+    xp = maxe.maxe_permute_gather(cperm, x)
+    yP = torch.empty(M, dtype=vdt, device="cuda")
+    yN = torch.empty(M, dtype=vdt, device="cuda")
+    yF = torch.empty(M, dtype=vdt, device="cuda")
+
+    def step_perm():
+        maxe.maxe_spmv(hP, xp, yP, permuted=True)
+
+    def step_plain():
+        maxe.maxe_spmv(hN, x, yN, permuted=True)
+
+    def step_full():
+        maxe.maxe_spmv(hP, x, yF)
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms_perm = timed_steps(step_perm, args.steps, args.warmup, world, args.graph_len)
+    clk = clocks.stop()
+    ms_plain = timed_steps(step_plain, args.steps, args.warmup, world, args.graph_len)
+    ms_full = timed_steps(step_full, max(args.steps // 4, 1), args.warmup, world, args.graph_len)
+    fl_perm = flushed_launch_ms(step_perm)
+    fl_plain = flushed_launch_ms(step_plain)
+
+    bytes_step = alg_bytes(M, N, Z, vb, xb, xb)
+    gbs = bytes_step / (ms_perm * 1e-3) / 1e9
+    gbs_plain = bytes_step / (ms_plain * 1e-3) / 1e9
+    hbm, src = peaks()
+
+    # ---- spot parity of the timed result against the oracle (sampled rows)
+    nrp, ncol, nval, _, _ = hP.csr()
+    rows = np.random.default_rng(0).choice(M, size=min(M, 4000), replace=False)
+    ref = oracle.spmv_rows(nrp.cpu().numpy(), ncol.cpu().numpy(),
+                           nval.cpu().numpy() if dtype != "bf16" else nval.cpu().view(torch.int16).numpy(),
+                           W.DTYPE_CODE[dtype], xp.cpu().double().numpy(), rows)
+    got = yP.cpu().double().numpy()[rows]
+    spot_err = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+
+    # ---- end to end through the public API with host buffers
+    x_host = x.cpu().pin_memory()
+    y_host = torch.empty(M, dtype=vdt).pin_memory()
+    x_dev = torch.empty_like(x)
+    y_dev = torch.empty(M, dtype=vdt, device="cuda")
+
+    def step_e2e():
+        x_dev.copy_(x_host, non_blocking=True)
+        maxe.maxe_spmv(hP, x_dev, y_dev)
+        y_host.copy_(y_dev, non_blocking=True)
+
+    ms_e2e = timed_steps(step_e2e, max(args.steps // 4, 1), args.warmup, world, graph_len=1)
+    e2e_gbs = bytes_step / (ms_e2e * 1e-3) / 1e9
+
+    traffic, rev = traffic_from_profile("spmv_chunk_powerlaw1M_f32.md")
+    if rev != KERNEL_REVISION:
+        traffic = None
+
+    out = {
+        "metric": METRIC, "value": round(gbs * world, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_perm, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": desc, "rows": M, "nnz": Z, "seed": args.seed,
+                   "variant": "permuted R-C (rows and columns), vectors in permuted space",
+                   "l2": "inputs larger than L2 (matrix %.0f MB > 129 MB); x', y' stay L2-resident across steps"
+                         % (bytes_step / 1e6),
+                   "timing": f"CUDA graph of {args.graph_len} steps replayed, CUDA events, max over ranks",
+                   "parallelism": "replicas only" if world > 1 else "single GPU"},
+        "plain": {"value": round(gbs_plain * world, 3), "unit": "GB/s", "ms_per_step": ms_plain,
+                  "frac": round(gbs_plain / hbm, 4)},
+        "permuted_over_plain": round(ms_plain / ms_perm, 4),
+        "flushed_l2_launch_ms": {"permuted": fl_perm, "plain": fl_plain},
+        "full_path": {"value": round(bytes_step / (ms_full * 1e-3) / 1e9, 3), "unit": "GB/s",
+                      "ms_per_step": ms_full, "what": "y = A x in the original space: x gather + SpMV with fused "
+                                                      "y scatter (algorithmic bytes of the product only)"},
+        "preprocess_ms": {"build_permutation_rows_and_cols": t_perm, "permute_csr": t_pcsr,
+                          "nnz_entropy_64x64": t_ent},
+        "entropy_64x64": {"plain": H_plain, "permuted": H_perm, "max": 12.0},
+        "spot_rel_l2_vs_oracle": spot_err,
+        "roofline": {"bound": "hbm", "achieved": round(gbs, 3), "peak": hbm, "unit": "GB/s",
+                     "frac": round(gbs / hbm, 4), "traffic": traffic, "peak_source": src,
+                     "bytes_per_launch": bytes_step},
+        "e2e": {"value": round(e2e_gbs * world, 3), "unit": "GB/s", "h2d_bytes_per_step": N * xb,
+                "d2h_bytes_per_step": M * xb, "ms_per_step": ms_e2e},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "context": "paper: ~15% gain from randomization on AMD GPU-CPU systems (FP64, rocSPARSE); context only",
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_cpu, reps = cpu_baseline(tuple(a.cpu().numpy() if a.dtype != torch.bfloat16 else
+                                         a.cpu().view(torch.int16).numpy() for a in (nrp, ncol, nval)),
+                                   xp.cpu().double().numpy(), W.DTYPE_CODE[dtype], args.cpu_seconds)
+        out["cpu_baseline"] = {"value": round(bytes_step / t_cpu / 1e9, 4), "unit": "GB/s", "cores": 1,
+                               "kind": "oracle", "sample": f"full permuted matrix, {reps} products, FP64 oracle"}
+    if rank == 0:
+        print(json.dumps(out))
+    hP.close()
+    hN.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * maxe.h -- C ABI of libmaxe.so: entropy-maximising random permutation of a
+ * sparse matrix and CSR SpMV/SpMM on the permuted matrix, for NVIDIA GB300
+ * (sm_103a).  Jain, Bustany, Fraisse, Benipal, Gaitonde, D'Alberto,
+ * "Entropy Maximization in Sparse Matrix by Vector Multiplication", arXiv 2308.00106.
+ *
+ * The method (Section 1, Eq. 1):  (P_r y) = (P_r A P_c) (P_c^{-1} x).
+ * Permutation convention used everywhere: perm[new] = old.  Hence
+ *   A'[i', j'] = A[rperm[i'], cperm[j']],   x'[j'] = x[cperm[j']],   y[rperm[i']] = y'[i'].
+ *
+ * Conventions of every entry point
+ *   - Pointers marked (device) are CUDA device pointers of the current device;
+ *     (host) are ordinary host pointers.  Arrays are dense, contiguous, and
+ *     owned by the caller unless stated otherwise.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Every call is stream-ordered and returns without synchronising, except
+ *     maxe_nnz_entropy, maxe_power_iteration and maxe_device_status, which
+ *     synchronise `stream` because they return a host value.
+ *   - Every call returns a maxe_status.  Argument checks run on the host before
+ *     any launch; a failing check launches nothing.  Launch errors surface as
+ *     MAXE_ERR_CUDA; asynchronous kernel errors surface on the next
+ *     synchronising call.  No C++ exception crosses the ABI.
+ *   - Index type is int32: rows, cols and nnz must each be <= INT32_MAX - 64.
+ *   - Device-side waits are bounded: a wait that runs out records
+ *     MAXE_ERR_TIMEOUT, the kernel returns, and maxe_device_status reports it.
+ *   - Results are deterministic: the same inputs, seed and handle give the same
+ *     bits on every run.
+ */
+#ifndef MAXE_H
+#define MAXE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MAXE_API __attribute__((visibility("default")))
+#else
+#define MAXE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MAXE_OK = 0,
+  MAXE_ERR_INVALID = 1,     /* bad argument (checked on the host, nothing launched) */
+  MAXE_ERR_OOM = 2,         /* the allocator returned NULL */
+  MAXE_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  MAXE_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+  MAXE_ERR_UNSUPPORTED = 5  /* valid request the library does not implement */
+} maxe_status;
+
+/* Stored value type of a matrix.  Vectors are FP64 for MAXE_F64 matrices and
+ * FP32 otherwise; accumulation is FP64 for MAXE_F64 and FP32 otherwise. */
+typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
+
+/* Flags of maxe_spmv / maxe_spmm: x and y are already in the permuted space
+ * (x' and y' of Eq. 1), so no vector permutation is done.  This is the
+ * iterative use the paper has in mind (the matrix is reused, Section 1). */
+#define MAXE_VEC_PERMUTED 0x1u
+/* Flag of maxe_permute_csr: check on the device that rowptr is monotone, columns
+ * are in range and perms are bijections (synchronises; MAXE_ERR_INVALID on failure). */
+#define MAXE_VALIDATE 0x2u
+
+/* Device memory allocator used for everything a handle owns and for scratch.
+ * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
+ * NULL; free(ptr, ctx, stream) releases it.  Passing NULL where a
+ * `const maxe_allocator*` is expected selects cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx, void* stream);
+  void (*free)(void* ptr, void* ctx, void* stream);
+  void* ctx;
+} maxe_allocator;
+
+/* A CSR matrix (Section 2: arrays V, COL, ROW): row i holds entries
+ * rowptr[i] .. rowptr[i+1]-1; col / val hold their columns and values.
+ * All pointers are (device), caller-owned, read-only for the library.
+ * rowptr has rows+1 entries, rowptr[0] = 0, rowptr[rows] = nnz. */
+typedef struct {
+  int32_t rows, cols;
+  int64_t nnz;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const void* val;
+  maxe_dtype dtype;
+} maxe_csr;
+
+/* Opaque, library-owned permuted matrix: the CSR of A' = P_r A P_c with
+ * ascending columns, the permutations, and the work partition of the SpMV
+ * kernel.  Owned arrays come from the allocator given at creation. */
+typedef struct maxe_handle maxe_handle;
+
+/* a1 + a2.  Random permutation of 0..n-1 (Section 3; seeded per the
+ * "Measuring" section's repeated runs).  key(seed, tag, i) is output number
+ * 2*i + tag + 1 of SplitMix64 seeded with `seed`; perm lists 0..n-1 in
+ * ascending (key, i) order.  tag 0 is used for rows, 1 for columns.
+ * perm: (device) int32[n], written.  alloc: scratch allocator (nullable).
+ * Errors: INVALID if n < 0, tag not in {0,1}, or perm NULL with n > 0. */
+MAXE_API maxe_status maxe_build_permutation(uint64_t seed, int32_t n, int32_t tag, int32_t* perm,
+                                   const maxe_allocator* alloc, void* stream);
+
+/* inv[perm[i]] = i (Eq. 1 needs P^{-1}).  perm, inv: (device) int32[n].
+ * perm must be a bijection (not checked here; see MAXE_VALIDATE). */
+MAXE_API maxe_status maxe_invert_permutation(const int32_t* perm, int32_t n, int32_t* inv, void* stream);
+
+/* a5.  Vector permutation of Eq. 1.  gather: out[i] = in[perm[i]] (x' = P_c^{-1} x);
+ * scatter: out[perm[i]] = in[i] (y = P_r^{-1} y').  elem_bytes in {2, 4, 8};
+ * in, out: (device) arrays of n elements, must not overlap. */
+MAXE_API maxe_status maxe_permute_gather(const int32_t* perm, int32_t n, int32_t elem_bytes, const void* in,
+                                void* out, void* stream);
+MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_t elem_bytes, const void* in,
+                                 void* out, void* stream);
+
+/* a3.  Build the permuted matrix A' = P_r A P_c (Eq. 1) in CSR with ascending
+ * columns (Section 2): new row i' is old row rperm[i']; old column c becomes
+ * cinv[c]; each row is then sorted by new column (stable).  Values are copied
+ * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
+ * (the "plain" matrix).  The handle keeps its own copies of the permutations.
+ * flags: 0 or MAXE_VALIDATE.  *out receives the new handle.
+ * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
+MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
+                             uint32_t flags, const maxe_allocator* alloc, void* stream,
+                             maxe_handle** out);
+
+/* Borrow the permuted CSR arrays (device pointers owned by the handle, valid
+ * until maxe_handle_destroy).  rperm/cperm (nullable outputs) receive the
+ * handle's permutation arrays, NULL for identity. */
+MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, const int32_t** rperm,
+                            const int32_t** cperm);
+
+/* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;
+ * hierarchical grids of Section 5).  counts[br*gc + bc] is the number of
+ * stored entries (i, j) of the handle's matrix with floor(i*gr/rows) = br and
+ * floor(j*gc/cols) = bc; H = -sum_{c>0} p log_base p with p = c / nnz
+ * (H = 0 when nnz = 0).  1 <= gr <= rows, 1 <= gc <= cols, base > 1.
+ * H_host: (host) receives H.  counts_dev: (device) int64[gr*gc] or NULL.
+ * alloc: scratch allocator (nullable).  Synchronises `stream`. */
+MAXE_API maxe_status maxe_nnz_entropy(const maxe_handle* h, int32_t gr, int32_t gc, double base, double* H_host,
+                             int64_t* counts_dev, const maxe_allocator* alloc, void* stream);
+
+/* a6 + a5.  y = A x (Section 2, CSR product) through the permuted matrix:
+ * without MAXE_VEC_PERMUTED, x is gathered to x' = P_c^{-1} x in handle-owned
+ * scratch, y' = A' x' is computed, and y[rperm[i']] = y'[i'] is written in the
+ * product's epilogue, so y = A x.  With MAXE_VEC_PERMUTED, y = A' x directly.
+ * x: (device) cols elements, y: (device) rows elements; FP64 for MAXE_F64
+ * handles, FP32 otherwise.  x and y must not overlap.  Calls on one handle
+ * without MAXE_VEC_PERMUTED share its x' scratch: do not overlap them in time. */
+MAXE_API maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uint32_t flags, void* stream);
+
+/* a7.  Y = A X for k right-hand sides (1 <= k <= 64).  X: (device) row-major
+ * cols x k with leading dimension ldx >= k; Y: (device) row-major rows x k,
+ * ldy >= k.  Element type and flags as for maxe_spmv.  Without
+ * MAXE_VEC_PERMUTED, rows of X are gathered into handle-owned scratch. */
+MAXE_API maxe_status maxe_spmm(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y,
+                      int64_t ldy, uint32_t flags, void* stream);
+
+/* Power iteration on a square handle, in the original space (v <- A v / ||A v||_2,
+ * `steps` times from v0, then lambda = v^T A v).  Not in the paper: it is the
+ * iterative reuse of the matrix that the paper's preconditioning analogy
+ * assumes (Section 1).  v0, v_out: (device) rows elements of the handle's
+ * vector type; lambda_host: (host).  Synchronises `stream`. */
+MAXE_API maxe_status maxe_power_iteration(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
+                                 double* lambda_host, void* stream);
+
+/* Release a handle and everything it owns (through its allocator, on the
+ * stream given at creation).  NULL is accepted. */
+MAXE_API maxe_status maxe_handle_destroy(maxe_handle* h);
+
+/* Synchronise `stream`, then return and clear the device-side status:
+ * MAXE_ERR_TIMEOUT if a bounded wait ran out since the last call, else MAXE_OK
+ * (or MAXE_ERR_CUDA if the stream reported an error). */
+MAXE_API maxe_status maxe_device_status(void* stream);
+
+/* Human-readable name of a status code. */
+MAXE_API const char* maxe_status_str(maxe_status s);
+
+/* Library version as "major.minor.patch". */
+MAXE_API const char* maxe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAXE_H */

@@ -1,0 +1,61 @@
+// handle.cuh -- layout of the library-owned permuted matrix (not part of the ABI).
+//
+// HBM layout of a handle (all int32 indices):
+//   rowptr  [rows + 1 + kRowptrPad]        row pointers of A' = P_r A P_c
+//   col     [nnz_pad]                      columns, ascending per row, zero padded
+//   val     [nnz_pad]                      values (f64 / f32 / bf16 bits), zero padded
+//   chunk_row [nq + 1]                     SpMV work partition (see spmv.cu)
+//   rperm, cperm [rows], [cols]            copies of the permutations (or NULL)
+//   xbuf                                   x' = P_c^{-1} x scratch for original-space calls
+// nnz_pad rounds nnz up to kPadElems so that every fixed-size chunk of the
+// SpMV pipeline can be fetched with one aligned bulk copy.
+#pragma once
+
+#include "internal.cuh"
+
+struct maxe_handle {
+  int32_t rows = 0, cols = 0;
+  int64_t nnz = 0, nnz_pad = 0;
+  maxe_dtype dtype = MAXE_F32;
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  void* val = nullptr;
+  int32_t* rperm = nullptr;
+  int32_t* cperm = nullptr;
+  int32_t* chunk_row = nullptr;
+  int32_t nq = 0;
+  void* xbuf = nullptr;  // cols * k_cap vector elements
+  int32_t xbuf_k = 0;
+  maxe::Allocator al;
+  int device = 0;
+  int sms = 0;
+  unsigned* status = nullptr;
+};
+
+namespace maxe {
+
+constexpr int kChunk = 2048;  // nnz per SpMV pipeline chunk
+
+inline int value_bytes(maxe_dtype d) { return d == MAXE_F64 ? 8 : (d == MAXE_F32 ? 4 : 2); }
+inline int vector_bytes(maxe_dtype d) { return d == MAXE_F64 ? 8 : 4; }
+
+// spmv.cu
+maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st);
+// Y = A' X (rows of Y optionally scattered through yperm).  X: cols x k (ldx),
+// Y: rows x k (ldy), vector element type of the handle.
+maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                        const int32_t* yperm, cudaStream_t st);
+
+// entropy.cu
+maxe_status entropy_run(const maxe_handle* h, int32_t gr, int32_t gc, double base, double* H_host,
+                        int64_t* counts_dev, const Allocator& al, cudaStream_t st);
+
+// permute_csr.cu
+maxe_status permute_csr_run(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm, uint32_t flags,
+                            maxe_handle* h, cudaStream_t st);
+
+// power.cu
+maxe_status power_iteration_run(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
+                                double* lambda_host, cudaStream_t st);
+
+}  // namespace maxe

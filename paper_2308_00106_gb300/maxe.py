@@ -1,0 +1,325 @@
+"""Thin ctypes binding of libmaxe.so (C ABI in include/maxe.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Torch provides device memory (its caching allocator is handed
+to the library as a ``maxe_allocator``) and the current CUDA stream.  There is
+no CPU fallback: if the library is missing or no GPU is visible, these calls
+raise.
+
+Function names follow the C entry points.  Permutations use perm[new] = old
+(Eq. 1 of arXiv 2308.00106):  A' = P_r A P_c,  x' = x[cperm],  y[rperm] = y'.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+MAXE_OK, MAXE_ERR_INVALID, MAXE_ERR_OOM, MAXE_ERR_CUDA, MAXE_ERR_TIMEOUT, MAXE_ERR_UNSUPPORTED = range(6)
+MAXE_F64, MAXE_F32, MAXE_BF16 = 0, 1, 2
+MAXE_VEC_PERMUTED = 0x1
+MAXE_VALIDATE = 0x2
+
+DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
+VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
+VEC_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.float32}
+
+EXPORTS = [
+    "maxe_build_permutation", "maxe_invert_permutation", "maxe_permute_gather", "maxe_permute_scatter",
+    "maxe_permute_csr", "maxe_handle_csr", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmm", "maxe_power_iteration",
+    "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
+]
+
+
+class MaxeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)}")
+        self.status = status
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)),
+                ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)),
+                ("ctx", ctypes.c_void_p)]
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("dtype", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+_live: dict[int, torch.Tensor] = {}  # allocations handed to the library
+
+
+def _torch_alloc(nbytes, ctx, stream):
+    try:
+        t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
+    except Exception:  # out of memory -> NULL -> MAXE_ERR_OOM
+        return None
+    p = t.data_ptr()
+    _live[p] = t
+    return p
+
+
+def _torch_free(ptr, ctx, stream):
+    if ptr:
+        _live.pop(int(ptr), None)
+
+
+_ALLOC = _Allocator(_Allocator._fields_[0][1](_torch_alloc), _Allocator._fields_[1][1](_torch_free), None)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libmaxe.so; raises if it has not been built (no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libmaxe.so not built ({_build.LIB}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        st = ctypes.c_int
+        sig = {
+            "maxe_build_permutation": [ctypes.c_uint64, I32, I32, P, P, P],
+            "maxe_invert_permutation": [P, I32, P, P],
+            "maxe_permute_gather": [P, I32, I32, P, P, P],
+            "maxe_permute_scatter": [P, I32, I32, P, P, P],
+            "maxe_permute_csr": [ctypes.POINTER(_Csr), P, P, U32, P, P, ctypes.POINTER(P)],
+            "maxe_handle_csr": [P, ctypes.POINTER(_Csr), ctypes.POINTER(P), ctypes.POINTER(P)],
+            "maxe_nnz_entropy": [P, I32, I32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), P, P, P],
+            "maxe_spmv": [P, P, P, U32, P],
+            "maxe_spmm": [P, I32, P, I64, P, I64, U32, P],
+            "maxe_power_iteration": [P, P, I32, P, ctypes.POINTER(ctypes.c_double), P],
+            "maxe_handle_destroy": [P],
+            "maxe_device_status": [P],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = st
+        lib.maxe_status_str.argtypes = [ctypes.c_int]
+        lib.maxe_status_str.restype = ctypes.c_char_p
+        lib.maxe_version.argtypes = []
+        lib.maxe_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def status_str(s: int) -> str:
+    try:
+        return load().maxe_status_str(s).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _check(s: int, what: str):
+    if s != MAXE_OK:
+        raise MaxeError(s, what)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class _DevArray:
+    """__cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def _view(ptr: int | None, n: int, dtype: torch.dtype) -> torch.Tensor | None:
+    if not ptr:
+        return None
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    if dtype == torch.bfloat16:
+        return torch.as_tensor(_DevArray(ptr, n, "<i2"), device="cuda").view(torch.bfloat16)
+    ts = {torch.int32: "<i4", torch.float32: "<f4", torch.float64: "<f8"}[dtype]
+    return torch.as_tensor(_DevArray(ptr, n, ts), device="cuda")
+
+
+class Handle:
+    """Library-owned permuted matrix A' = P_r A P_c (opaque maxe_handle*)."""
+
+    def __init__(self, ptr: int, rows: int, cols: int, nnz: int, dtype: int, keep):
+        self.ptr = ptr
+        self.rows, self.cols, self.nnz, self.dtype = rows, cols, nnz, dtype
+        self._keep = keep
+
+    @property
+    def vec_dtype(self) -> torch.dtype:
+        return VEC_TORCH[self.dtype]
+
+    def csr(self):
+        """(rowptr, col, val, rperm, cperm) as zero-copy torch views of the handle's arrays."""
+        v = _Csr()
+        rp, cp = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().maxe_handle_csr(ctypes.c_void_p(self.ptr), ctypes.byref(v), ctypes.byref(rp), ctypes.byref(cp)),
+               "maxe_handle_csr")
+        return (_view(v.rowptr, self.rows + 1, torch.int32), _view(v.col, self.nnz, torch.int32),
+                _view(v.val, self.nnz, VAL_TORCH[self.dtype]), _view(rp.value, self.rows, torch.int32),
+                _view(cp.value, self.cols, torch.int32))
+
+    def close(self):
+        if self.ptr:
+            load().maxe_handle_destroy(ctypes.c_void_p(self.ptr))
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ entry points
+
+def maxe_build_permutation(seed: int, n: int, tag: int, perm: torch.Tensor | None = None, stream=None):
+    """perm[new] = old, sorted by key(seed, tag, i) (Section 3)."""
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    _dev(perm, torch.int32, "perm")
+    _check(load().maxe_build_permutation(ctypes.c_uint64(seed & (2**64 - 1)), n, tag, _ptr(perm),
+                                         ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream))),
+           "maxe_build_permutation")
+    return perm
+
+
+def maxe_invert_permutation(perm: torch.Tensor, stream=None):
+    _dev(perm, torch.int32, "perm")
+    inv = torch.empty_like(perm)
+    _check(load().maxe_invert_permutation(_ptr(perm), perm.numel(), _ptr(inv), ctypes.c_void_p(_stream(stream))),
+           "maxe_invert_permutation")
+    return inv
+
+
+def maxe_permute_gather(perm: torch.Tensor, x: torch.Tensor, stream=None):
+    """out[i] = x[perm[i]]  (x' = P_c^{-1} x)."""
+    _dev(perm, torch.int32, "perm")
+    out = torch.empty(perm.numel(), dtype=x.dtype, device="cuda")
+    _check(load().maxe_permute_gather(_ptr(perm), perm.numel(), x.element_size(), _ptr(x), _ptr(out),
+                                      ctypes.c_void_p(_stream(stream))), "maxe_permute_gather")
+    return out
+
+
+def maxe_permute_scatter(perm: torch.Tensor, y: torch.Tensor, stream=None):
+    """out[perm[i]] = y[i]  (y = P_r^{-1} y')."""
+    _dev(perm, torch.int32, "perm")
+    out = torch.empty(perm.numel(), dtype=y.dtype, device="cuda")
+    _check(load().maxe_permute_scatter(_ptr(perm), perm.numel(), y.element_size(), _ptr(y), _ptr(out),
+                                       ctypes.c_void_p(_stream(stream))), "maxe_permute_scatter")
+    return out
+
+
+def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
+                     rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
+                     stream=None) -> Handle:
+    """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity."""
+    code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[val.dtype]
+    _dev(rowptr, torch.int32, "rowptr")
+    _dev(col, torch.int32, "col")
+    _dev(val, val.dtype, "val")
+    if rperm is not None:
+        _dev(rperm, torch.int32, "rperm")
+    if cperm is not None:
+        _dev(cperm, torch.int32, "cperm")
+    A = _Csr(rows, cols, col.numel(), rowptr.data_ptr(), col.data_ptr() if col.numel() else None,
+             val.data_ptr() if val.numel() else None, code)
+    out = ctypes.c_void_p()
+    _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), MAXE_VALIDATE if validate else 0,
+                                   ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
+           "maxe_permute_csr")
+    return Handle(out.value, rows, cols, col.numel(), code, keep=None)
+
+
+def maxe_nnz_entropy(h: Handle, gr: int, gc: int, base: float = 2.0, counts: bool = True, stream=None):
+    """(H, counts[gr, gc] int64 or None) of the nonzero block-grid histogram (Section 4)."""
+    H = ctypes.c_double()
+    cnt = torch.empty(gr * gc, dtype=torch.int64, device="cuda") if counts else None
+    _check(load().maxe_nnz_entropy(ctypes.c_void_p(h.ptr), gr, gc, float(base), ctypes.byref(H), _ptr(cnt),
+                                   ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream))), "maxe_nnz_entropy")
+    return H.value, (cnt.view(gr, gc) if counts else None)
+
+
+def maxe_spmv(h: Handle, x: torch.Tensor, y: torch.Tensor | None = None, permuted: bool = False, stream=None):
+    """y = A x (original space), or y' = A' x' with permuted=True (MAXE_VEC_PERMUTED)."""
+    _dev(x, h.vec_dtype, "x")
+    if x.numel() != h.cols:
+        raise ValueError("x has the wrong length")
+    if y is None:
+        y = torch.empty(h.rows, dtype=h.vec_dtype, device="cuda")
+    _dev(y, h.vec_dtype, "y")
+    _check(load().maxe_spmv(ctypes.c_void_p(h.ptr), _ptr(x), _ptr(y), MAXE_VEC_PERMUTED if permuted else 0,
+                            ctypes.c_void_p(_stream(stream))), "maxe_spmv")
+    return y
+
+
+def maxe_spmm(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, permuted: bool = False, stream=None):
+    """Y = A X for row-major X (cols x k); permuted=True keeps both in the permuted space."""
+    if X.dim() != 2 or X.shape[0] != h.cols or X.stride(1) != 1:
+        raise ValueError("X must be (cols, k) with unit column stride")
+    if X.dtype != h.vec_dtype or not X.is_cuda:
+        raise TypeError("X has the wrong dtype/device")
+    k = X.shape[1]
+    if Y is None:
+        Y = torch.empty(h.rows, k, dtype=h.vec_dtype, device="cuda")
+    if Y.stride(1) != 1 or Y.shape != (h.rows, k):
+        raise ValueError("Y must be (rows, k) with unit column stride")
+    _check(load().maxe_spmm(ctypes.c_void_p(h.ptr), k, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0),
+                            MAXE_VEC_PERMUTED if permuted else 0, ctypes.c_void_p(_stream(stream))), "maxe_spmm")
+    return Y
+
+
+def maxe_power_iteration(h: Handle, v0: torch.Tensor, steps: int, stream=None):
+    """(lambda, v) after `steps` normalised products in the original space."""
+    _dev(v0, h.vec_dtype, "v0")
+    v = torch.empty_like(v0)
+    lam = ctypes.c_double()
+    _check(load().maxe_power_iteration(ctypes.c_void_p(h.ptr), _ptr(v0), steps, _ptr(v), ctypes.byref(lam),
+                                       ctypes.c_void_p(_stream(stream))), "maxe_power_iteration")
+    return lam.value, v
+
+
+def maxe_device_status(stream=None) -> int:
+    return load().maxe_device_status(ctypes.c_void_p(_stream(stream)))
+
+
+def maxe_version() -> str:
+    return load().maxe_version().decode()
+
+
+def from_csr(A, rperm=None, cperm=None, validate=False, stream=None) -> Handle:
+    """Handle from a workloads.CSR already on the GPU."""
+    return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream)
