@@ -42,7 +42,7 @@ void release(maxe_handle* h) {
   if (!h) return;
   const Allocator& al = h->al;
   al.put(h->xbuf);
-  al.put(h->chunk_row);
+  al.put(h->wrow);
   al.put(h->cperm);
   al.put(h->rperm);
   al.put(h->val);

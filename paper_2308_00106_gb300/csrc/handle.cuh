@@ -4,11 +4,12 @@
 //   rowptr  [rows + 1 + kRowptrPad]        row pointers of A' = P_r A P_c
 //   col     [nnz_pad]                      columns, ascending per row, zero padded
 //   val     [nnz_pad]                      values (f64 / f32 / bf16 bits), zero padded
-//   chunk_row [nq + 1]                     SpMV work partition (see spmv.cu)
+//   wrow    [nW + 1]                       SpMV work partition: first row of each warp range
 //   rperm, cperm [rows], [cols]            copies of the permutations (or NULL)
 //   xbuf                                   x' = P_c^{-1} x scratch for original-space calls
-// nnz_pad rounds nnz up to kPadElems so that every fixed-size chunk of the
-// SpMV pipeline can be fetched with one aligned bulk copy.
+// nnz_pad leaves at least two 128-entry pieces of zeros after the last entry,
+// so the SpMV warps can load whole aligned pieces (and prefetch one ahead)
+// without a bounds test.
 #pragma once
 
 #include "internal.cuh"
@@ -22,8 +23,9 @@ struct maxe_handle {
   void* val = nullptr;
   int32_t* rperm = nullptr;
   int32_t* cperm = nullptr;
-  int32_t* chunk_row = nullptr;
-  int32_t nq = 0;
+  int32_t* wrow = nullptr;
+  int32_t nW = 0;
+  int64_t range = 0;  // entries per warp range
   void* xbuf = nullptr;  // cols * k_cap vector elements
   int32_t xbuf_k = 0;
   maxe::Allocator al;
@@ -34,12 +36,11 @@ struct maxe_handle {
 
 namespace maxe {
 
-constexpr int kChunk = 2048;  // nnz per SpMV pipeline chunk
-
 inline int value_bytes(maxe_dtype d) { return d == MAXE_F64 ? 8 : (d == MAXE_F32 ? 4 : 2); }
 inline int vector_bytes(maxe_dtype d) { return d == MAXE_F64 ? 8 : 4; }
 
 // spmv.cu
+int64_t spmv_pad_elems();
 maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st);
 // Y = A' X (rows of Y optionally scattered through yperm).  X: cols x k (ldx),
 // Y: rows x k (ldy), vector element type of the handle.

@@ -14,7 +14,7 @@ namespace maxe {
 
 // ----------------------------------------------------------------- limits
 constexpr int64_t kMaxIndex = 2147483647LL - 64;  // rows, cols, nnz bound
-constexpr int kPadElems = 4096;  // col/val arrays owned by a handle are padded to this multiple
+constexpr int kPadElems = 4096;  // col/val arrays owned by a handle are rounded up to this multiple
 constexpr int kRowptrPad = 8;    // extra rowptr entries owned by a handle
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded device waits give up after 2 s
 
@@ -201,6 +201,8 @@ struct ScratchSet {
 size_t scan_scratch_elems(int64_t n);
 maxe_status scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total_out,
                                int32_t* scratch, cudaStream_t st);
+// *p = v on the stream.
+maxe_status set_i32(int32_t* p, int32_t v, cudaStream_t st);
 // first[g] = min{ i in [0, npos) : pos[i] >= g*H + off } (npos if none), g in [0, nb].
 maxe_status bucket_lower_bounds(const int32_t* pos, int64_t npos, int64_t H, int64_t off, int64_t nb,
                                 int32_t* first, cudaStream_t st);

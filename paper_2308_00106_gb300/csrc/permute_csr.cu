@@ -260,7 +260,7 @@ maxe_status permute_csr_run(const maxe_csr* A, const int32_t* rperm, const int32
 
   // owned arrays
   const int vb = value_bytes(A->dtype);
-  h->nnz_pad = round_up(std::max<int64_t>(Z, 1), kPadElems);
+  h->nnz_pad = round_up(Z + spmv_pad_elems(), kPadElems);
   h->rowptr = static_cast<int32_t*>(al.get(static_cast<size_t>(M + 1 + kRowptrPad) * sizeof(int32_t)));
   h->col = static_cast<int32_t*>(al.get(static_cast<size_t>(h->nnz_pad) * sizeof(int32_t)));
   h->val = al.get(static_cast<size_t>(h->nnz_pad) * vb);

@@ -122,7 +122,15 @@ __global__ void bucket_lb_kernel(const int32_t* __restrict__ pos, int64_t npos, 
   for (int64_t g = lo; g <= hi; ++g) first[g] = static_cast<int32_t>(i);
 }
 
+__global__ void set_i32_kernel(int32_t* p, int32_t v) { *p = v; }
+
 }  // namespace
+
+maxe_status set_i32(int32_t* p, int32_t v, cudaStream_t st) {
+  set_i32_kernel<<<1, 1, 0, st>>>(p, v);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  return MAXE_OK;
+}
 
 size_t scan_scratch_elems(int64_t n) { return static_cast<size_t>(ceil_div(n > 0 ? n : 1, kScanTile)) + 1; }
 

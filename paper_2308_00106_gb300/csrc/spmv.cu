@@ -1,50 +1,46 @@
 // spmv.cu -- nnz-balanced CSR SpMV / SpMM on the permuted matrix (Section 2:
 // y_i = sum_{l in ROW[i]:ROW[i+1]} V[l] * x[COL[l]];  Eq. 1 for the permuted form).
 //
-// Work partition.  The nonzeros are cut into fixed chunks of kChunk = 2048
-// entries.  Chunk q owns the rows whose last entry falls inside it (rows with
-// rowptr[r+1] in (q*C, (q+1)*C]; chunk 0 also owns leading empty rows), so
-// every row is written by exactly one chunk:  chunk_row[q] = first row with
-// rowptr[r+1] > q*C.  A launch of G persistent CTAs gives CTA c the chunk range
-// [c*nq/G, (c+1)*nq/G): equal nonzeros per CTA whatever the row lengths, which
-// is the load balance the paper's laggard argument asks of the permutation
-// (Section 1), obtained here without it.
+// Work partition (built once per handle).  The nonzeros are cut into nW ranges
+// of H entries; warp w owns the rows that START in [w*H, (w+1)*H) (wrow[w] =
+// first row with rowptr[r] >= w*H) and streams all of their entries, so every
+// warp does H entries give or take one row, whatever the row-length law, and
+// no partial sum ever crosses between warps: the load balance the paper's
+// laggard argument (Section 1) asks of the permutation, obtained without it.
+// nW is the number of warps the GPU keeps resident, so one launch is one wave.
 //
-// Pipeline per CTA (288 threads): one producer warp streams each chunk's COL and
-// VAL slices and its slice of ROW into shared memory with 1-D bulk copies (TMA),
-// S stages deep, completion on mbarriers, L2 evict-first (the matrix is read once
-// per product).  Eight consumer warps, each thread holding 8 consecutive entries:
-//   1. mark the first entry of every row that starts in the chunk (bit flags);
-//   2. gather x[COL] (through L1/L2) and form the products in registers;
-//   3. segmented inclusive scan of the products: serial over the thread's 8
-//      entries, warp shuffles across lanes, one shared-memory step across warps;
-//      the partial row that crosses from the previous chunk enters as a carry;
-//   4. y[row] = scan value at the row's last entry, for every owned row
-//      (empty rows get 0; rows may be scattered through rperm, which fuses the
-//      y = P_r^{-1} y' step of Eq. 1 into the epilogue).
-// A row that starts before the CTA's first chunk is summed directly from HBM by
-// the CTA before its pipeline starts, so CTAs never exchange partial sums and
-// the result depends only on the matrix, the chunk size and G: it is
-// deterministic.
+// Per warp, the entries go by in pieces of 256 (8 consecutive entries per lane):
+//   * COL and VAL of each piece land in the warp's own shared-memory ring by
+//     1-D bulk copies (TMA, L2 evict-first: the matrix is read once per
+//     product), kStages pieces ahead, completion on one mbarrier per stage, so
+//     prefetching costs no registers;
+//   * the row pointers of the rows that end in the piece (32 per load, one
+//     piece ahead) mark the row starts in a 256-bit shared-memory bitmap;
+//   * x[COL] is gathered through L1/L2 and multiplied in registers;
+//   * a segmented inclusive scan (serial over the lane's 8 entries, 5 shuffle
+//     steps across lanes) sums each row; the partial row that runs on into the
+//     next piece is kept as the warp's carry;
+//   * each row that ends in the piece reads its sum back from the scan and is
+//     written once, optionally through rperm (y = P_r^{-1} y' fused into the
+//     epilogue).
+// The result depends only on the matrix and the partition: deterministic.
 //
-// SpMM reuses the pipeline: X rows are gathered VW columns at a time (float4,
-// float2/double2), and the scan runs on VW-wide vectors, one pass per group of
-// VW columns.
+// SpMM: X rows are gathered VW columns at a time (float4 / float2 / double2),
+// and the scan runs on VW-wide vectors, one pass per group of VW columns.
 #include <algorithm>
+#include <climits>
 
 #include "handle.cuh"
 
 namespace maxe {
 namespace {
 
-constexpr int kConsumerWarps = 8;
-constexpr int kConsumers = kConsumerWarps * 32;  // 256
-constexpr int kThreads = kConsumers + 32;        // + producer warp
-constexpr int kItems = 8;                        // entries per consumer thread
-constexpr int kRowCap = kChunk / 2 + 8;          // rowptr slice held in shared memory
-constexpr int kMaxK = 64;                        // right-hand sides per call
-constexpr int kBarConsumers = 1;                 // named barrier id
-static_assert(kConsumers * kItems == kChunk, "chunk = consumers x items");
+constexpr int kWarps = 8;        // warps per block
+constexpr int kThreads = kWarps * 32;
+constexpr int kItems = 8;                // consecutive entries per lane
+constexpr int kPiece = 32 * kItems;      // entries per warp step (256)
+constexpr int kStages = 2;               // bulk-copy ring depth per warp
+constexpr int kMaxK = 64;
 
 template <typename VT>
 struct Acc;
@@ -68,66 +64,11 @@ struct Params {
   const void* X;
   void* Y;
   const int32_t* yperm;
-  const int32_t* chunk_row;
+  const int32_t* wrow;
   unsigned* status;
-  int64_t ldx, ldy, Z;
-  int32_t k, M, nq;
+  int64_t ldx, ldy;
+  int32_t k, M, nW;
 };
-
-constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-template <typename VT, int VW, int S>
-struct Layout {
-  using AT = typename Acc<VT>::T;
-  static constexpr size_t col_off = 0;
-  static constexpr size_t val_off = col_off + size_t(S) * kChunk * 4;
-  static constexpr size_t rp_off = align16(val_off + size_t(S) * kChunk * sizeof(VT));
-  static constexpr size_t sums_off = align16(rp_off + size_t(S) * kRowCap * 4);
-  static constexpr size_t flags_off = align16(sums_off + size_t(kChunk) * VW * sizeof(AT));
-  static constexpr size_t wagg_off = align16(flags_off + (kChunk / 32) * 4);
-  static constexpr size_t waggf_off = align16(wagg_off + kConsumerWarps * VW * sizeof(AT));
-  static constexpr size_t carry_off = align16(waggf_off + kConsumerWarps * 4);
-  static constexpr size_t meta_off = align16(carry_off + (kMaxK + 4) * sizeof(AT));
-  static constexpr size_t bar_off = align16(meta_off + S * sizeof(int4));
-  static constexpr size_t bytes = bar_off + 2 * S * sizeof(uint64_t);
-};
-
-// ---- value / vector access ------------------------------------------------
-template <typename VT, typename AT>
-__device__ __forceinline__ AT to_acc(VT v) {
-  return static_cast<AT>(v);
-}
-template <>
-__device__ __forceinline__ float to_acc<uint16_t, float>(uint16_t v) {
-  return bf16_bits_to_float(v);
-}
-
-// 8 consecutive values from shared memory (16-byte aligned).
-template <typename VT, typename AT>
-__device__ __forceinline__ void load8(const VT* p, AT (&a)[kItems]);
-template <>
-__device__ __forceinline__ void load8<float, float>(const float* p, float (&a)[kItems]) {
-  const float4 u = reinterpret_cast<const float4*>(p)[0], v = reinterpret_cast<const float4*>(p)[1];
-  a[0] = u.x, a[1] = u.y, a[2] = u.z, a[3] = u.w, a[4] = v.x, a[5] = v.y, a[6] = v.z, a[7] = v.w;
-}
-template <>
-__device__ __forceinline__ void load8<double, double>(const double* p, double (&a)[kItems]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const double2 u = reinterpret_cast<const double2*>(p)[i];
-    a[2 * i] = u.x, a[2 * i + 1] = u.y;
-  }
-}
-template <>
-__device__ __forceinline__ void load8<uint16_t, float>(const uint16_t* p, float (&a)[kItems]) {
-  const uint4 u = reinterpret_cast<const uint4*>(p)[0];
-  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    a[2 * i] = __uint_as_float(w[i] << 16);
-    a[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-  }
-}
 
 template <int VW, typename AT>
 __device__ __forceinline__ void xload(const AT* __restrict__ X, int32_t c, int64_t ldx, int c0, int k, AT (&xv)[VW]) {
@@ -176,157 +117,166 @@ __device__ __forceinline__ void ystore(AT* __restrict__ Y, int64_t row, int64_t 
   }
 }
 
-// ---- producer warp --------------------------------------------------------
-template <typename VT, int VW, int S>
-__device__ __forceinline__ void produce(const Params& p, unsigned char* sm, int64_t q0, int64_t q1) {
-  using L = Layout<VT, VW, S>;
-  const int lane = threadIdx.x & 31;
-  int32_t* col_s = reinterpret_cast<int32_t*>(sm + L::col_off);
-  VT* val_s = reinterpret_cast<VT*>(sm + L::val_off);
-  int32_t* rp_s = reinterpret_cast<int32_t*>(sm + L::rp_off);
-  int4* meta = reinterpret_cast<int4*>(sm + L::meta_off);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + L::bar_off);
-  uint64_t* empty = full + S;
-  const VT* val_g = static_cast<const VT*>(p.val);
-  const uint64_t pol = policy_evict_first();
-  const int64_t n = q1 - q0;
-  int abort = 0;
-  for (int64_t base = 0; base < n && !abort; base += 32) {
-    const int64_t qa = q0 + base + lane;
-    const int32_t cra = (qa <= q1) ? p.chunk_row[qa] : 0;
-    const int32_t crb = (qa + 1 <= q1) ? p.chunk_row[qa + 1] : 0;
-    const int cnt = static_cast<int>(n - base < 32 ? n - base : 32);
-    for (int j = 0; j < cnt; ++j) {
-      const int32_t ra = __shfl_sync(0xffffffffu, cra, j);
-      const int32_t rb = __shfl_sync(0xffffffffu, crb, j);
-      if (lane == 0) {
-        const int64_t i = base + j;
-        const int s = static_cast<int>(i % S);
-        if (i >= S && !mbar_wait_bounded(&empty[s], static_cast<uint32_t>(((i / S) & 1) ^ 1), p.status)) abort = 1;
-        if (!abort) {
-          const int64_t q = q0 + i;
-          const int32_t lo = ra & ~3;
-          const int32_t hi = (rb + 4) & ~3;
-          const int32_t nr = hi - lo;
-          const int big = nr > kRowCap;
-          meta[s] = make_int4(ra, rb, lo, big);
-          const uint32_t bytes = kChunk * 4u + kChunk * static_cast<uint32_t>(sizeof(VT)) + (big ? 0u : nr * 4u);
-          mbar_arrive_expect_tx(&full[s], bytes);
-          bulk_g2s(col_s + static_cast<size_t>(s) * kChunk, p.col + q * kChunk, kChunk * 4u, &full[s], pol);
-          bulk_g2s(val_s + static_cast<size_t>(s) * kChunk, val_g + q * kChunk,
-                   kChunk * static_cast<uint32_t>(sizeof(VT)), &full[s], pol);
-          if (!big) bulk_g2s(rp_s + static_cast<size_t>(s) * kRowCap, p.rowptr + lo, nr * 4u, &full[s], pol);
-        }
-      }
-      abort = __shfl_sync(0xffffffffu, abort, 0);
-      if (abort) break;
+// Per-warp shared memory: an S-stage ring of COL/VAL pieces filled by 1-D bulk
+// copies (TMA) with one mbarrier per stage, the row-start bitmap of the current
+// piece, the scanned sums it is read back from, and the carries of the k columns.
+template <typename VT, int VW>
+struct alignas(16) WarpSmem {
+  using AT = typename Acc<VT>::T;
+  int32_t col[kStages][kPiece];
+  VT val[kStages][kPiece];
+  AT sums[kPiece * VW];
+  uint32_t flags[kPiece / 32];
+  AT carry[kMaxK + 4];
+  uint64_t full[kStages];
+};
+
+template <typename VT, int VW>
+constexpr size_t block_smem() {
+  return sizeof(WarpSmem<VT, VW>) * kWarps;
+}
+
+template <typename VT>
+__device__ __forceinline__ void lds_vals(const VT* p, typename Acc<VT>::T (&a)[kItems]);
+template <>
+__device__ __forceinline__ void lds_vals<float>(const float* p, float (&a)[kItems]) {
+#pragma unroll
+  for (int i = 0; i < kItems / 4; ++i) {
+    const float4 u = reinterpret_cast<const float4*>(p)[i];
+    a[4 * i] = u.x, a[4 * i + 1] = u.y, a[4 * i + 2] = u.z, a[4 * i + 3] = u.w;
+  }
+}
+template <>
+__device__ __forceinline__ void lds_vals<double>(const double* p, double (&a)[kItems]) {
+#pragma unroll
+  for (int i = 0; i < kItems / 2; ++i) {
+    const double2 u = reinterpret_cast<const double2*>(p)[i];
+    a[2 * i] = u.x, a[2 * i + 1] = u.y;
+  }
+}
+template <>
+__device__ __forceinline__ void lds_vals<uint16_t>(const uint16_t* p, float (&a)[kItems]) {
+#pragma unroll
+  for (int i = 0; i < kItems / 8; ++i) {
+    const uint4 u = reinterpret_cast<const uint4*>(p)[i];
+    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[8 * i + 2 * q] = __uint_as_float(w4[q] << 16);
+      a[8 * i + 2 * q + 1] = __uint_as_float(w4[q] & 0xFFFF0000u);
     }
   }
 }
 
-// ---- consumer warps -------------------------------------------------------
-template <typename VT, int VW, int S>
-__device__ __forceinline__ void consume(const Params& p, unsigned char* sm, int64_t q0, int64_t q1) {
-  using L = Layout<VT, VW, S>;
-  using AT = typename Acc<VT>::T;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int32_t* col_s = reinterpret_cast<const int32_t*>(sm + L::col_off);
-  const VT* val_s = reinterpret_cast<const VT*>(sm + L::val_off);
-  const int32_t* rp_s = reinterpret_cast<const int32_t*>(sm + L::rp_off);
-  AT* sums = reinterpret_cast<AT*>(sm + L::sums_off);
-  uint32_t* flags = reinterpret_cast<uint32_t*>(sm + L::flags_off);
-  AT* wagg = reinterpret_cast<AT*>(sm + L::wagg_off);
-  int* waggf = reinterpret_cast<int*>(sm + L::waggf_off);
-  AT* carry = reinterpret_cast<AT*>(sm + L::carry_off);
-  const int4* meta = reinterpret_cast<const int4*>(sm + L::meta_off);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + L::bar_off);
-  uint64_t* empty = full + S;
+template <typename VT, int VW>
+__device__ __forceinline__ void issue_piece(WarpSmem<VT, VW>& ws, int s, const Params& p, int32_t base,
+                                            uint64_t pol) {
+  mbar_arrive_expect_tx(&ws.full[s], kPiece * (4u + static_cast<uint32_t>(sizeof(VT))));
+  bulk_g2s(ws.col[s], p.col + base, kPiece * 4u, &ws.full[s], pol);
+  bulk_g2s(ws.val[s], static_cast<const VT*>(p.val) + base, kPiece * static_cast<uint32_t>(sizeof(VT)), &ws.full[s],
+           pol);
+}
 
+// resident blocks per SM the register budget is cut for (VW = 1 matters most)
+template <typename VT, int VW>
+constexpr int min_blocks() {
+  return sizeof(typename Acc<VT>::T) == 8 ? (VW == 1 ? 3 : 2) : (VW == 1 ? 4 : (VW == 2 ? 3 : 2));
+}
+
+template <typename VT, int VW>
+__global__ void __launch_bounds__(kThreads, min_blocks<VT, VW>()) spmm_warp_kernel(Params p) {
+  using AT = typename Acc<VT>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarps + wib;
+  if (w >= p.nW) return;
+  WarpSmem<VT, VW>& ws = reinterpret_cast<WarpSmem<VT, VW>*>(smem_raw)[wib];
   const AT* X = static_cast<const AT*>(p.X);
   AT* Y = static_cast<AT*>(p.Y);
-  const VT* val_g = static_cast<const VT*>(p.val);
   const int k = p.k;
   const int ngroups = (k + VW - 1) / VW;
 
-  // Carry into the first chunk: the part of its first row lying before it.
-  {
-    const int64_t qc0 = q0 * kChunk;
-    const int32_t r = p.chunk_row[q0];
-    const int64_t st = (r < p.M) ? static_cast<int64_t>(p.rowptr[r]) : qc0;
-    for (int g = 0; g < ngroups; ++g) {
-      AT acc[VW];
-#pragma unroll
-      for (int u = 0; u < VW; ++u) acc[u] = AT(0);
-      for (int64_t e = st + tid; e < qc0; e += kConsumers) {
-        AT xv[VW];
-        xload<VW>(X, p.col[e], p.ldx, g * VW, k, xv);
-        const AT a = to_acc<VT, AT>(val_g[e]);
-#pragma unroll
-        for (int u = 0; u < VW; ++u) acc[u] += a * xv[u];
-      }
-#pragma unroll
-      for (int u = 0; u < VW; ++u)
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], d);
-      if (lane == 0)
-#pragma unroll
-        for (int u = 0; u < VW; ++u) wagg[w * VW + u] = acc[u];
-      named_bar(kBarConsumers, kConsumers);
-      if (tid < VW) {
-        AT t = AT(0);
-        for (int ww = 0; ww < kConsumerWarps; ++ww) t += wagg[ww * VW + tid];
-        carry[g * VW + tid] = t;
-      }
-      named_bar(kBarConsumers, kConsumers);
-    }
-    if (tid < kChunk / 32) flags[tid] = 0u;
-    named_bar(kBarConsumers, kConsumers);
+  const int32_t r_hi = p.wrow[w + 1];
+  int32_t r = p.wrow[w];  // first row of the range not yet written
+  const int32_t e_lo = p.rowptr[r];
+  const int32_t e_hi = p.rowptr[r_hi];
+  const int32_t base0 = e_lo & ~7;  // 16-byte aligned for every value type
+  const int32_t npieces = (e_hi > base0) ? (e_hi - base0 + kPiece - 1) / kPiece : 0;
+  const uint64_t pol = policy_evict_first();
+  if (lane == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&ws.full[s], 1);
+    fence_mbar_init();
   }
+  for (int c = lane; c < ngroups * VW; c += 32) ws.carry[c] = AT(0);
+  if (lane < kPiece / 32) ws.flags[lane] = 0u;
+  __syncwarp();
+  if (lane == 0)
+    for (int s = 0; s < kStages && s < npieces; ++s) issue_piece(ws, s, p, base0 + s * kPiece, pol);
 
-  const int64_t n = q1 - q0;
-  for (int64_t i = 0; i < n; ++i) {
-    const int s = static_cast<int>(i % S);
-    bool ok = mbar_wait_bounded(&full[s], static_cast<uint32_t>((i / S) & 1), p.status);
-    ok = named_bar_and(kBarConsumers, kConsumers, ok);
-    if (!ok) return;
-    const int4 m = meta[s];
-    const int32_t ra = m.x, rb = m.y;
-    const int32_t* rp = m.w ? p.rowptr : (rp_s + static_cast<size_t>(s) * kRowCap - m.z);
-    const int64_t qC = (q0 + i) * kChunk;
+  int32_t r_start = e_lo;  // first entry of row r
+  int32_t end0 = (r + lane < r_hi) ? __ldg(p.rowptr + r + 1 + lane) : INT_MAX;
 
-    // 1. row-start flags of the chunk
-    for (int32_t r = ra + tid; r <= rb && r < p.M; r += kConsumers) {
-      const int64_t st = rp[r];
-      if (st >= qC && st < qC + kChunk) {
-        const bool nonempty = (r < rb) ? (rp[r + 1] > st) : true;
-        if (nonempty) {
-          const int off = static_cast<int>(st - qC);
-          atomicOr(&flags[off >> 5], 1u << (off & 31));
-        }
+  for (int32_t i = 0; i < npieces; ++i) {
+    const int s = i % kStages;
+    const int32_t base = base0 + i * kPiece;
+    // rows ending in this piece: flags in the bitmap, count, last end
+    int nend = 0;
+    int32_t last_o = -1;
+    {
+      int32_t end = end0;
+      while (true) {
+        const int32_t o = end - base;  // end <= INT_MAX and base >= 0: no overflow
+        const bool in = o <= kPiece;
+        const int n = __popc(__ballot_sync(0xffffffffu, in));
+        if (in && o >= 1 && o < kPiece) atomicOr(&ws.flags[o >> 5], 1u << (o & 31));
+        if (n > 0) last_o = __shfl_sync(0xffffffffu, o, n - 1);
+        nend += n;
+        if (n < 32) break;
+        const int32_t rr = r + nend + lane;
+        end = (rr < r_hi) ? __ldg(p.rowptr + rr + 1) : INT_MAX;
       }
     }
-    named_bar(kBarConsumers, kConsumers);
-    const uint32_t f8 = (flags[tid >> 2] >> ((tid & 3) * 8)) & 0xFFu;
+    const int32_t rn = r + nend;
+    const int32_t end_first = end0;
+    end0 = (rn + lane < r_hi) ? __ldg(p.rowptr + rn + 1 + lane) : INT_MAX;  // next piece, one step ahead
+    __syncwarp();
+    const uint32_t fw = (ws.flags[(kItems * lane) >> 5] >> ((kItems * lane) & 31)) & ((1u << kItems) - 1u);
+    const int first_flag = fw ? __ffs(fw) - 1 : kItems;
 
+    bool ok = mbar_wait_bounded(&ws.full[s], static_cast<uint32_t>((i / kStages) & 1), p.status);
+    if (!__all_sync(0xffffffffu, ok)) return;
     int32_t cj[kItems];
     AT a[kItems];
-    {
-      const int4* cp = reinterpret_cast<const int4*>(col_s + static_cast<size_t>(s) * kChunk + kItems * tid);
-      const int4 c0v = cp[0], c1v = cp[1];
-      cj[0] = c0v.x, cj[1] = c0v.y, cj[2] = c0v.z, cj[3] = c0v.w;
-      cj[4] = c1v.x, cj[5] = c1v.y, cj[6] = c1v.z, cj[7] = c1v.w;
-      load8<VT, AT>(val_s + static_cast<size_t>(s) * kChunk + kItems * tid, a);
+#pragma unroll
+    for (int q = 0; q < kItems / 4; ++q) {
+      const int4 u = reinterpret_cast<const int4*>(ws.col[s] + kItems * lane)[q];
+      cj[4 * q] = u.x, cj[4 * q + 1] = u.y, cj[4 * q + 2] = u.z, cj[4 * q + 3] = u.w;
     }
-    const int64_t e0 = qC + kItems * tid;
-    const int nvalid = static_cast<int>(p.Z - e0 < 0 ? 0 : (p.Z - e0 > kItems ? kItems : p.Z - e0));
+    lds_vals<VT>(ws.val[s] + kItems * lane, a);
+    __syncwarp();
+    if (lane < kPiece / 32) ws.flags[lane] = 0u;  // every lane has its flag bits
+    // entries outside [e_lo, e_hi) belong to other warps (first and last piece only)
+    uint32_t vmask = (1u << kItems) - 1u;
+    if (!(base >= e_lo && base + kPiece <= e_hi)) {
+#pragma unroll
+      for (int j = 0; j < kItems; ++j) {
+        const int32_t e = base + kItems * lane + j;
+        if (e < e_lo || e >= e_hi) vmask &= ~(1u << j);
+      }
+    }
+    // the stage is in registers: refill it with piece i + kStages
+    __syncwarp();
+    if (lane == 0 && i + kStages < npieces) {
+      fence_proxy_async_smem();
+      issue_piece(ws, s, p, base + kStages * kPiece, pol);
+    }
 
     for (int g = 0; g < ngroups; ++g) {
       const int c0 = g * VW;
-      // 2. products
       AT v[kItems][VW];
 #pragma unroll
       for (int j = 0; j < kItems; ++j) {
-        if (j < nvalid) {
+        if ((vmask >> j) & 1u) {
           AT xv[VW];
           xload<VW>(X, cj[j], p.ldx, c0, k, xv);
 #pragma unroll
@@ -336,14 +286,12 @@ __device__ __forceinline__ void consume(const Params& p, unsigned char* sm, int6
           for (int u = 0; u < VW; ++u) v[j][u] = AT(0);
         }
       }
-      // 3a. serial segmented scan over the thread's entries
 #pragma unroll
       for (int j = 1; j < kItems; ++j)
-        if (!((f8 >> j) & 1u))
+        if (!((fw >> j) & 1u))
 #pragma unroll
           for (int u = 0; u < VW; ++u) v[j][u] += v[j - 1][u];
-      // 3b. warp-level segmented scan of the thread aggregates
-      int F = f8 != 0u;
+      int F = fw != 0u;
       AT V[VW];
 #pragma unroll
       for (int u = 0; u < VW; ++u) V[u] = v[kItems - 1][u];
@@ -360,134 +308,124 @@ __device__ __forceinline__ void consume(const Params& p, unsigned char* sm, int6
           F |= Fu;
         }
       }
-      int Fe = __shfl_up_sync(0xffffffffu, F, 1);
-      AT Ve[VW];
-#pragma unroll
-      for (int u = 0; u < VW; ++u) Ve[u] = __shfl_up_sync(0xffffffffu, V[u], 1);
-      if (lane == 0) {
-        Fe = 0;
-#pragma unroll
-        for (int u = 0; u < VW; ++u) Ve[u] = AT(0);
-      }
-      if (lane == 31) {
-        waggf[w] = F;
-#pragma unroll
-        for (int u = 0; u < VW; ++u) wagg[w * VW + u] = V[u];
-      }
-      named_bar(kBarConsumers, kConsumers);
-      if (g == 0 && tid < kChunk / 32) flags[tid] = 0u;  // every thread has its f8 by now
-      // 3c. prefix = carry (+) warps before w (+) lanes before this one
+      const int Fe = __shfl_up_sync(0xffffffffu, F, 1);
       AT P[VW];
 #pragma unroll
-      for (int u = 0; u < VW; ++u) P[u] = carry[c0 + u];
-      for (int ww = 0; ww < w; ++ww) {
-        const bool fw = waggf[ww] != 0;
-#pragma unroll
-        for (int u = 0; u < VW; ++u) P[u] = fw ? wagg[ww * VW + u] : P[u] + wagg[ww * VW + u];
+      for (int u = 0; u < VW; ++u) {
+        const AT Ve = __shfl_up_sync(0xffffffffu, V[u], 1);
+        const AT cin = ws.carry[c0 + u];
+        P[u] = (lane == 0) ? cin : (Fe ? Ve : cin + Ve);
       }
-#pragma unroll
-      for (int u = 0; u < VW; ++u) P[u] = Fe ? Ve[u] : P[u] + Ve[u];
-      const int first_flag = f8 ? __ffs(f8) - 1 : kItems;
 #pragma unroll
       for (int j = 0; j < kItems; ++j)
         if (j < first_flag)
 #pragma unroll
           for (int u = 0; u < VW; ++u) v[j][u] += P[u];
-      AT* sp = sums + static_cast<size_t>(kItems * tid) * VW;
 #pragma unroll
       for (int j = 0; j < kItems; ++j)
 #pragma unroll
-        for (int u = 0; u < VW; ++u) sp[j * VW + u] = v[j][u];
-      named_bar(kBarConsumers, kConsumers);
-      // 4. owned rows
-      for (int32_t r = ra + tid; r < rb; r += kConsumers) {
-        const int32_t st = rp[r], en = rp[r + 1];
-        AT out[VW];
-        if (en > st) {
-          const AT* src = sums + static_cast<size_t>(en - 1 - qC) * VW;
+        for (int u = 0; u < VW; ++u) ws.sums[(kItems * lane + j) * VW + u] = v[j][u];
+      __syncwarp();
+      // rows that end in the piece
+      int32_t prev_end = r_start;
+      for (int b = 0; b < nend; b += 32) {
+        const int32_t rr = r + b + lane;
+        int32_t end = end_first;
+        if (b > 0) end = (rr < r_hi) ? __ldg(p.rowptr + rr + 1) : INT_MAX;
+        int32_t start = __shfl_up_sync(0xffffffffu, end, 1);
+        if (lane == 0) start = prev_end;
+        if (b + lane < nend) {
+          AT out[VW];
+          if (end > start) {
+            const AT* src = ws.sums + (end - base - 1) * VW;
 #pragma unroll
-          for (int u = 0; u < VW; ++u) out[u] = src[u];
-        } else {
+            for (int u = 0; u < VW; ++u) out[u] = src[u];
+          } else {
 #pragma unroll
-          for (int u = 0; u < VW; ++u) out[u] = AT(0);
+            for (int u = 0; u < VW; ++u) out[u] = AT(0);
+          }
+          const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
+          ystore<VW>(Y, row, p.ldy, c0, k, out);
         }
-        const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[r]) : static_cast<int64_t>(r);
-        ystore<VW>(Y, row, p.ldy, c0, k, out);
+        prev_end = __shfl_sync(0xffffffffu, end, 31);
       }
-      if (tid == 0) {
-        const bool cont = (rb < p.M) && (rp[rb] < qC + kChunk);
-#pragma unroll
-        for (int u = 0; u < VW; ++u) carry[c0 + u] = cont ? sums[static_cast<size_t>(kChunk - 1) * VW + u] : AT(0);
-      }
-      named_bar(kBarConsumers, kConsumers);
+      // partial row running on into the next piece
+      if (lane < VW) ws.carry[c0 + lane] = (last_o == kPiece) ? AT(0) : ws.sums[(kPiece - 1) * VW + lane];
+      __syncwarp();
     }
-    if (tid == 0) mbar_arrive(&empty[s]);
+    if (nend > 0) r_start = base + last_o;
+    r = rn;
+  }
+  // rows left over are empty (their entries were all consumed)
+  for (int32_t rr = r + lane; rr < r_hi; rr += 32) {
+    const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
+    for (int c = 0; c < k; ++c) Y[row * p.ldy + c] = AT(0);
   }
 }
-
-template <typename VT, int VW, int S>
-__global__ void __launch_bounds__(kThreads) spmm_chunk_kernel(Params p) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  using L = Layout<VT, VW, S>;
-  const int64_t G = gridDim.x;
-  const int64_t q0 = static_cast<int64_t>(blockIdx.x) * p.nq / G;
-  const int64_t q1 = static_cast<int64_t>(blockIdx.x + 1) * p.nq / G;
-  if (q0 >= q1) return;
-  if (threadIdx.x == 0) {
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + L::bar_off);
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&full[S + s], 1);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x >= kConsumers)
-    produce<VT, VW, S>(p, sm, q0, q1);
-  else
-    consume<VT, VW, S>(p, sm, q0, q1);
-}
-
-constexpr int kStages = 3;
 
 template <typename VT, int VW>
-maxe_status launch_variant(const Params& p, int sms, cudaStream_t st) {
-  using L = Layout<VT, VW, kStages>;
-  auto kern = spmm_chunk_kernel<VT, VW, kStages>;
-  static int occ = -1;  // resident CTAs per SM for this variant
-  if (occ < 0) {
-    MAXE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::bytes)));
-    int o = 0;
-    MAXE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreads, L::bytes));
-    occ = o > 0 ? o : 1;
+maxe_status prepare_variant() {
+  static bool done = false;  // the attribute is per function and process
+  if (!done) {
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_warp_kernel<VT, VW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(block_smem<VT, VW>())));
+    done = true;
   }
-  const int64_t G = std::min<int64_t>(p.nq, static_cast<int64_t>(sms) * occ);
-  kern<<<static_cast<unsigned>(G), kThreads, L::bytes, st>>>(p);
+  return MAXE_OK;
+}
+
+template <typename VT, int VW>
+maxe_status launch_variant(const Params& p, cudaStream_t st) {
+  MAXE_TRY((prepare_variant<VT, VW>()));
+  const unsigned grid = static_cast<unsigned>(ceil_div(p.nW, kWarps));
+  spmm_warp_kernel<VT, VW><<<grid, kThreads, block_smem<VT, VW>(), st>>>(p);
   MAXE_CUDA_TRY(cudaGetLastError());
   return MAXE_OK;
 }
 
 template <typename VT>
-maxe_status launch_dtype(const Params& p, int vw, int sms, cudaStream_t st) {
-  if (vw == 1) return launch_variant<VT, 1>(p, sms, st);
-  if (vw == 2) return launch_variant<VT, 2>(p, sms, st);
+maxe_status launch_dtype(const Params& p, int vw, cudaStream_t st) {
+  if (vw == 1) return launch_variant<VT, 1>(p, st);
+  if (vw == 2) return launch_variant<VT, 2>(p, st);
   if constexpr (sizeof(typename Acc<VT>::T) == 4) {
-    if (vw == 4) return launch_variant<VT, 4>(p, sms, st);
+    if (vw == 4) return launch_variant<VT, 4>(p, st);
   }
   return MAXE_ERR_UNSUPPORTED;
 }
 
+template <typename VT>
+int resident_warps(int sms) {
+  int blocks = 0;
+  if (prepare_variant<VT, 1>() != MAXE_OK ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, spmm_warp_kernel<VT, 1>, kThreads,
+                                                    block_smem<VT, 1>()) != cudaSuccess ||
+      blocks < 1) {
+    cudaGetLastError();
+    blocks = 1;
+  }
+  return sms * blocks * kWarps;
+}
+
 }  // namespace
 
+int64_t spmv_pad_elems() { return kPiece * 2 + 8; }
+
 maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st) {
-  const int64_t nq = std::max<int64_t>(1, ceil_div(h->nnz, kChunk));
-  h->chunk_row = static_cast<int32_t*>(h->al.get(static_cast<size_t>(nq + 1) * sizeof(int32_t)));
-  if (!h->chunk_row) return MAXE_ERR_OOM;
-  h->nq = static_cast<int32_t>(nq);
-  // chunk_row[q] = min{ r : rowptr[r+1] >= q*C + 1 }, then chunk 0 owns leading empty rows.
-  MAXE_TRY(bucket_lower_bounds(h->rowptr + 1, h->rows, kChunk, 1, nq, h->chunk_row, st));
-  MAXE_CUDA_TRY(cudaMemsetAsync(h->chunk_row, 0, sizeof(int32_t), st));
-  return MAXE_OK;
+  int target = 0;
+  switch (h->dtype) {
+    case MAXE_F64: target = resident_warps<double>(h->sms); break;
+    case MAXE_F32: target = resident_warps<float>(h->sms); break;
+    case MAXE_BF16: target = resident_warps<uint16_t>(h->sms); break;
+  }
+  const int64_t H = std::max<int64_t>(kPiece, ceil_div(std::max<int64_t>(h->nnz, 1), std::max(target, 1)));
+  const int64_t nW = std::max<int64_t>(1, ceil_div(h->nnz, H));
+  h->wrow = static_cast<int32_t*>(h->al.get(static_cast<size_t>(nW + 1) * sizeof(int32_t)));
+  if (!h->wrow) return MAXE_ERR_OOM;
+  h->nW = static_cast<int32_t>(nW);
+  h->range = H;
+  // wrow[w] = min{ r : rowptr[r] >= w*H }; the last range also takes trailing empty rows
+  MAXE_TRY(bucket_lower_bounds(h->rowptr, h->rows, H, 0, nW, h->wrow, st));
+  return set_i32(h->wrow + nW, h->rows, st);
 }
 
 maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,
@@ -500,14 +438,13 @@ maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t 
   p.X = X;
   p.Y = Y;
   p.yperm = yperm;
-  p.chunk_row = h->chunk_row;
+  p.wrow = h->wrow;
   p.status = h->status;
   p.ldx = ldx;
   p.ldy = ldy;
-  p.Z = h->nnz;
   p.k = k;
   p.M = h->rows;
-  p.nq = h->nq;
+  p.nW = h->nW;
   const int eb = vector_bytes(h->dtype);
   auto aligned = [&](int vw) {
     const uintptr_t a = static_cast<uintptr_t>(vw) * eb;
@@ -522,12 +459,9 @@ maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t 
       vw = 2;
   }
   switch (h->dtype) {
-    case MAXE_F64:
-      return launch_dtype<double>(p, vw, h->sms, st);
-    case MAXE_F32:
-      return launch_dtype<float>(p, vw, h->sms, st);
-    case MAXE_BF16:
-      return launch_dtype<uint16_t>(p, vw, h->sms, st);
+    case MAXE_F64: return launch_dtype<double>(p, vw, st);
+    case MAXE_F32: return launch_dtype<float>(p, vw, st);
+    case MAXE_BF16: return launch_dtype<uint16_t>(p, vw, st);
   }
   return MAXE_ERR_INVALID;
 }
