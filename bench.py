@@ -61,7 +61,7 @@ def traffic_from_profile(name):
     return t, kernel_rev
 
 
-KERNEL_REVISION = "spmm_warp_kernel r1"  # bump whenever the SpMV kernel changes
+KERNEL_REVISION = "spmm_warp_kernel r2"  # bump whenever the SpMV kernel changes
 
 
 class Clocks:
@@ -305,9 +305,9 @@ def main():
     rperm = maxe.maxe_build_permutation(args.seed, M, 0)
     cperm = maxe.maxe_build_permutation(args.seed, N, 1)
     ev[1].record()
-    hP = maxe.from_csr(A, rperm, cperm)
+    hP = maxe.from_csr(A, rperm, cperm, autotune=True)
     ev[2].record()
-    hN = maxe.from_csr(A)
+    hN = maxe.from_csr(A, autotune=True)
     ev[3].record()
     torch.cuda.synchronize()
     t_perm, t_pcsr = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
@@ -392,11 +392,12 @@ def main():
         "plain": {"value": round(gbs_plain * world, 3), "unit": "GB/s", "ms_per_step": ms_plain,
                   "frac": round(gbs_plain / hbm, 4)},
         "permuted_over_plain": round(ms_plain / ms_perm, 4),
+        "kernel_variant": {"permuted_items_per_lane": hP.items_per_lane(), "plain_items_per_lane": hN.items_per_lane()},
         "flushed_l2_launch_ms": {"permuted": fl_perm, "plain": fl_plain},
         "full_path": {"value": round(bytes_step / (ms_full * 1e-3) / 1e9, 3), "unit": "GB/s",
                       "ms_per_step": ms_full, "what": "y = A x in the original space: x gather + SpMV with fused "
                                                       "y scatter (algorithmic bytes of the product only)"},
-        "preprocess_ms": {"build_permutation_rows_and_cols": t_perm, "permute_csr": t_pcsr,
+        "preprocess_ms": {"build_permutation_rows_and_cols": t_perm, "permute_csr_with_autotune": t_pcsr,
                           "nnz_entropy_64x64": t_ent},
         "entropy_64x64": {"plain": H_plain, "permuted": H_perm, "max": 12.0},
         "spot_rel_l2_vs_oracle": spot_err,

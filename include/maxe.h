@@ -62,6 +62,13 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
 /* Flag of maxe_permute_csr: check on the device that rowptr is monotone, columns
  * are in range and perms are bijections (synchronises; MAXE_ERR_INVALID on failure). */
 #define MAXE_VALIDATE 0x2u
+/* Flag of maxe_permute_csr: time the SpMV kernel variants (8 or 16 entries
+ * per lane) on this matrix and keep the faster one for the handle
+ * (synchronises; a few products of device time). */
+#define MAXE_AUTOTUNE 0x4u
+/* Flag of maxe_permute_csr: use the 16-entries-per-lane SpMV variant without
+ * timing (tuning override; MAXE_AUTOTUNE takes precedence). */
+#define MAXE_ITEMS16 0x8u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -117,7 +124,8 @@ MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_
  * cinv[c]; each row is then sorted by new column (stable).  Values are copied
  * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
  * (the "plain" matrix).  The handle keeps its own copies of the permutations.
- * flags: 0 or MAXE_VALIDATE.  *out receives the new handle.
+ * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16.  *out receives the new handle.
+ * Synchronises `stream` once (to size the pass over rows longer than 2048).
  * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
 MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
                              uint32_t flags, const maxe_allocator* alloc, void* stream,
@@ -128,6 +136,10 @@ MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, c
  * handle's permutation arrays, NULL for identity. */
 MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, const int32_t** rperm,
                             const int32_t** cperm);
+
+/* Entries per lane of the handle's SpMV kernel variant (8 or 16), as chosen
+ * by MAXE_AUTOTUNE / MAXE_ITEMS16 at creation.  items: (host). */
+MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;
  * hierarchical grids of Section 5).  counts[br*gc + bc] is the number of

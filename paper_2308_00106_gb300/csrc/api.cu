@@ -42,7 +42,8 @@ void release(maxe_handle* h) {
   if (!h) return;
   const Allocator& al = h->al;
   al.put(h->xbuf);
-  al.put(h->wrow);
+  al.put(h->wrow[1]);
+  al.put(h->wrow[0]);
   al.put(h->cperm);
   al.put(h->rperm);
   al.put(h->val);
@@ -125,7 +126,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (bad_size(A->rows) || bad_size(A->cols) || bad_size(A->nnz) || bad_dtype(A->dtype)) return MAXE_ERR_INVALID;
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return MAXE_ERR_INVALID;
   if (A->nnz > 0 && (A->rows == 0 || A->cols == 0)) return MAXE_ERR_INVALID;
-  if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE)) return MAXE_ERR_INVALID;
+  if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16)) return MAXE_ERR_INVALID;
   DeviceInfo di{};
   MAXE_TRY(device_info(&di));
   cudaStream_t st = as_stream(stream);
@@ -141,6 +142,8 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   h->status = di.status;
   maxe_status s = permute_csr_run(A, rperm, cperm, flags, h, st);
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
+  if (s == MAXE_OK && (flags & MAXE_ITEMS16)) h->spmv_items16 = 1;
+  if (s == MAXE_OK && (flags & MAXE_AUTOTUNE)) s = spmv_autotune(h, st);
   if (s != MAXE_OK) {
     release(h);
     return s;
@@ -160,6 +163,12 @@ maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view, const int32_t*
   view->dtype = h->dtype;
   if (rperm) *rperm = h->rperm;
   if (cperm) *cperm = h->cperm;
+  return MAXE_OK;
+}
+
+maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
+  if (!h || !items) return MAXE_ERR_INVALID;
+  *items = h->spmv_items16 ? 16 : 8;
   return MAXE_OK;
 }
 

@@ -23,9 +23,9 @@ struct maxe_handle {
   void* val = nullptr;
   int32_t* rperm = nullptr;
   int32_t* cperm = nullptr;
-  int32_t* wrow = nullptr;
-  int32_t nW = 0;
-  int64_t range = 0;  // entries per warp range
+  int32_t* wrow[2] = {nullptr, nullptr};  // per SpMV variant (8 / 16 entries per lane)
+  int32_t nW[2] = {0, 0};
+  int spmv_items16 = 0;                    // chosen SpMV variant (autotuned or 0)
   void* xbuf = nullptr;  // cols * k_cap vector elements
   int32_t xbuf_k = 0;
   maxe::Allocator al;
@@ -44,8 +44,11 @@ int64_t spmv_pad_elems();
 maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st);
 // Y = A' X (rows of Y optionally scattered through yperm).  X: cols x k (ldx),
 // Y: rows x k (ldy), vector element type of the handle.
+// variant: -1 = the handle's choice, 0 / 1 = force 8 / 16 entries per lane.
 maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,
-                        const int32_t* yperm, cudaStream_t st);
+                        const int32_t* yperm, cudaStream_t st, int variant = -1);
+// Time the SpMV variants on this matrix and keep the faster (synchronises).
+maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st);
 
 // entropy.cu
 maxe_status entropy_run(const maxe_handle* h, int32_t gr, int32_t gc, double base, double* H_host,

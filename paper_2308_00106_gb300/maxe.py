@@ -23,6 +23,8 @@ MAXE_OK, MAXE_ERR_INVALID, MAXE_ERR_OOM, MAXE_ERR_CUDA, MAXE_ERR_TIMEOUT, MAXE_E
 MAXE_F64, MAXE_F32, MAXE_BF16 = 0, 1, 2
 MAXE_VEC_PERMUTED = 0x1
 MAXE_VALIDATE = 0x2
+MAXE_AUTOTUNE = 0x4
+MAXE_ITEMS16 = 0x8
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -30,7 +32,7 @@ VEC_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.
 
 EXPORTS = [
     "maxe_build_permutation", "maxe_invert_permutation", "maxe_permute_gather", "maxe_permute_scatter",
-    "maxe_permute_csr", "maxe_handle_csr", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmm", "maxe_power_iteration",
+    "maxe_permute_csr", "maxe_handle_csr", "maxe_handle_tuning", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmm", "maxe_power_iteration",
     "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
 ]
 
@@ -100,6 +102,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_permute_scatter": [P, I32, I32, P, P, P],
             "maxe_permute_csr": [ctypes.POINTER(_Csr), P, P, U32, P, P, ctypes.POINTER(P)],
             "maxe_handle_csr": [P, ctypes.POINTER(_Csr), ctypes.POINTER(P), ctypes.POINTER(P)],
+            "maxe_handle_tuning": [P, ctypes.POINTER(I32)],
             "maxe_nnz_entropy": [P, I32, I32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), P, P, P],
             "maxe_spmv": [P, P, P, U32, P],
             "maxe_spmm": [P, I32, P, I64, P, I64, U32, P],
@@ -192,6 +195,12 @@ class Handle:
                 _view(v.val, self.nnz, VAL_TORCH[self.dtype]), _view(rp.value, self.rows, torch.int32),
                 _view(cp.value, self.cols, torch.int32))
 
+    def items_per_lane(self) -> int:
+        """Entries per lane of the SpMV kernel variant this handle uses (8 or 16)."""
+        v = ctypes.c_int32()
+        _check(load().maxe_handle_tuning(ctypes.c_void_p(self.ptr), ctypes.byref(v)), "maxe_handle_tuning")
+        return v.value
+
     def close(self):
         if self.ptr:
             load().maxe_handle_destroy(ctypes.c_void_p(self.ptr))
@@ -245,7 +254,7 @@ def maxe_permute_scatter(perm: torch.Tensor, y: torch.Tensor, stream=None):
 
 def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
-                     stream=None) -> Handle:
+                     stream=None, autotune: bool = False, items16: bool = False) -> Handle:
     """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity."""
     code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[val.dtype]
     _dev(rowptr, torch.int32, "rowptr")
@@ -258,7 +267,8 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
     A = _Csr(rows, cols, col.numel(), rowptr.data_ptr(), col.data_ptr() if col.numel() else None,
              val.data_ptr() if val.numel() else None, code)
     out = ctypes.c_void_p()
-    _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), MAXE_VALIDATE if validate else 0,
+    flags = (MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
+    _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
     return Handle(out.value, rows, cols, col.numel(), code, keep=None)
@@ -320,6 +330,6 @@ def maxe_version() -> str:
     return load().maxe_version().decode()
 
 
-def from_csr(A, rperm=None, cperm=None, validate=False, stream=None) -> Handle:
+def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
-    return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream)
+    return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16)

@@ -112,10 +112,12 @@ def test_permute_csr_validate_rejects_bad_perm():
 
 @pytest.mark.parametrize("kind", EDGE_KINDS)
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
-def test_spmv_edges_original_and_permuted_space(kind, dtype):
+@pytest.mark.parametrize("items16", [False, True])
+def test_spmv_edges_original_and_permuted_space(kind, dtype, items16):
     A = edge_matrix(kind, dtype, seed=3)
     rperm, cperm = _perms(A, 11, "rc")
-    h = maxe.from_csr(A.to("cuda"), rperm, cperm)
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, items16=items16)
+    assert h.items_per_lane() == (16 if items16 else 8)
     x = W.vector(5, A.cols, "f64" if dtype == "f64" else "f32", "cuda")
     rp, co, va = A.numpy()
     y = maxe.maxe_spmv(h, x)  # y = A x through Eq. 1
@@ -198,6 +200,10 @@ def test_products_are_deterministic():
     assert torch.equal(y1, y2)
     h2 = maxe.from_csr(A, *_perms(A, 7, "rc"))
     assert torch.equal(maxe.maxe_spmv(h2, x), y1)
+    # the autotuned handle gives the oracle's result whichever variant it picks
+    h3 = maxe.from_csr(A, *_perms(A, 7, "rc"), autotune=True)
+    assert h3.items_per_lane() in (8, 16)
+    assert rel_l2(maxe.maxe_spmv(h3, x).cpu().numpy(), y1.cpu().numpy()) <= 1e-6
 
 
 # ----------------------------------------------------------------- entropy
