@@ -151,6 +151,28 @@ MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 MAXE_API maxe_status maxe_nnz_entropy(const maxe_handle* h, int32_t gr, int32_t gc, double base, double* H_host,
                              int64_t* counts_dev, const maxe_allocator* alloc, void* stream);
 
+/* Allocation-free form of maxe_nnz_entropy (the paper has no counterpart).
+ * Some callers cannot call cudaMalloc: for example a host framework that has
+ * reserved all device memory for its own pool and hands a plugin only its
+ * input and output buffers, or code on a path where cudaMalloc's implicit
+ * device-wide synchronisation is not allowed.  This entry point computes the
+ * same counts and H as maxe_nnz_entropy, and allocates nothing: its scratch is
+ * a static device array of 65536 32-bit counts plus one double (256 KiB),
+ * which every GPU that loads the library holds until the process exits.
+ * Arguments as for maxe_nnz_entropy (there is no allocator argument).
+ * Limits and behaviour:
+ *   - gr * gc must be <= 65536; larger grids return MAXE_ERR_INVALID.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the one array and leaves its counts in
+ *     it; each call clears the cells it uses before counting.  Calls that
+ *     overlap on the GPU (other streams, other host threads) race on the array
+ *     and give wrong results: serialise them.
+ *   - Synchronises `stream` (H is returned on the host). */
+MAXE_API maxe_status maxe_nnz_entropy_noalloc(const maxe_handle* h, int32_t gr, int32_t gc, double base,
+                                              double* H_host, int64_t* counts_dev, void* stream);
+
 /* a6 + a5.  y = A x (Section 2, CSR product) through the permuted matrix:
  * without MAXE_VEC_PERMUTED, x is gathered to x' = P_c^{-1} x in handle-owned
  * scratch, y' = A' x' is computed, and y[rperm[i']] = y'[i'] is written in the

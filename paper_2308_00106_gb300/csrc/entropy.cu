@@ -12,6 +12,7 @@
 // FP64 in a fixed order (deterministic).  Only rowptr and col are read:
 // 4 bytes per entry plus the row pointers.
 #include <algorithm>
+#include <mutex>
 
 #include "handle.cuh"
 
@@ -144,3 +145,62 @@ maxe_status entropy_run(const maxe_handle* h, int32_t gr, int32_t gc, double bas
 }
 
 }  // namespace maxe
+
+// ------------------------------------------------- allocation-free variant
+namespace {
+
+constexpr int64_t kNoAllocMaxBins = 65536;  // grid cells the static scratch holds (256 KiB of counts)
+
+// Scratch of maxe_nnz_entropy_noalloc: kNoAllocMaxBins 32-bit counts, then H.
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_entropy_scratch[kNoAllocMaxBins * sizeof(unsigned) + 256];
+
+// Device address of g_entropy_scratch, looked up once per device with that
+// device current (in host code the symbol is only a host-side stand-in).
+maxe_status noalloc_scratch(unsigned char** out) {
+  static std::mutex mu;
+  static unsigned char* addr[64] = {};
+  int dev = 0;
+  MAXE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return MAXE_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_entropy_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return MAXE_ERR_CUDA;
+    }
+    addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = addr[dev];
+  return MAXE_OK;
+}
+
+}  // namespace
+
+extern "C" maxe_status maxe_nnz_entropy_noalloc(const maxe_handle* h, int32_t gr, int32_t gc, double base,
+                                                double* H_host, int64_t* counts_dev, void* stream) {
+  using namespace maxe;
+  if (!h || !H_host) return MAXE_ERR_INVALID;
+  if (gr < 1 || gc < 1 || gr > h->rows || gc > h->cols || !(base > 1.0)) return MAXE_ERR_INVALID;
+  const int64_t nbins = static_cast<int64_t>(gr) * gc;
+  if (nbins > kNoAllocMaxBins) return MAXE_ERR_INVALID;
+  unsigned char* scratch = nullptr;
+  MAXE_TRY(noalloc_scratch(&scratch));
+  unsigned* counts = reinterpret_cast<unsigned*>(scratch);
+  double* Hd = reinterpret_cast<double*>(scratch + kNoAllocMaxBins * sizeof(unsigned));
+  cudaStream_t st = as_stream(stream);
+  // the array keeps the previous call's counts: clear the cells this call uses
+  MAXE_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(unsigned) * nbins, st));
+  if (h->nnz > 0) {
+    const int64_t grid = ceil_div(h->nnz, kHTile);
+    hist_kernel<<<static_cast<unsigned>(grid), kHThreads, 0, st>>>(h->rowptr, h->col, h->rows, h->cols, h->nnz, gr,
+                                                                    gc, counts);
+    MAXE_CUDA_TRY(cudaGetLastError());
+  }
+  entropy_kernel<<<1, kEThreads, 0, st>>>(counts, nbins, h->nnz, base, counts_dev, Hd);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  MAXE_CUDA_TRY(cudaMemcpyAsync(H_host, Hd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MAXE_CUDA_TRY(cudaStreamSynchronize(st));
+  return MAXE_OK;
+}
