@@ -189,6 +189,52 @@ MAXE_API maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uin
 MAXE_API maxe_status maxe_spmm(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y,
                       int64_t ldy, uint32_t flags, void* stream);
 
+/* a9.  Batched persistent SpMV/SpMM (many uneven matrices, each with its own
+ * k right-hand sides, in one launch per value type present).
+ *
+ * An item asks for Y = A' X on a handle: X (device) is in the permuted space
+ * (x' = x[cperm], rows of X gathered), row-major cols x k with leading
+ * dimension ldx >= k; Y (device) rows x k, ldy >= k, written in the permuted
+ * space, or through rperm into the original space with MAXE_BATCH_SCATTER_Y.
+ * 1 <= k <= 64.  Each handle carries a batch plan (entries per warp task and
+ * entries per lane), made at creation and retuned by maxe_batch_tune; it does
+ * not depend on the other items, so an item's result is bit-identical alone
+ * and in any mix.
+ *
+ * A batch object keeps the descriptor table in pinned host memory and uploads
+ * it on the stream right before the launch, so maxe_batch_run can be captured
+ * in a CUDA graph (capture after maxe_batch_set; replays use the table as set).
+ * A batch object serves one stream at a time; maxe_batch_run waits (on the
+ * host) until the previous run's table upload has executed before rewriting
+ * the staging. */
+#define MAXE_BATCH_SCATTER_Y 0x1u
+typedef struct maxe_batch maxe_batch;
+typedef struct {
+  const maxe_handle* h;
+  int32_t k;
+  const void* X;
+  int64_t ldx;
+  void* Y;
+  int64_t ldy;
+  uint32_t flags; /* 0 or MAXE_BATCH_SCATTER_Y */
+} maxe_batch_item;
+
+/* New batch object for up to `capacity` items (1 <= capacity <= 2^20).
+ * Device tables come from `alloc` (nullable); the host staging is pinned. */
+MAXE_API maxe_status maxe_batch_create(int32_t capacity, const maxe_allocator* alloc, void* stream, maxe_batch** out);
+/* Replace the item list (host array of n items, copied).  INVALID on bad items. */
+MAXE_API maxe_status maxe_batch_set(maxe_batch* b, const maxe_batch_item* items, int32_t n);
+/* Upload the table and launch the persistent kernel(s) on `stream`. */
+MAXE_API maxe_status maxe_batch_run(maxe_batch* b, void* stream);
+MAXE_API maxe_status maxe_batch_destroy(maxe_batch* b);
+/* Autotune the handle's batch plan for k right-hand sides: time single-item
+ * batches over entries-per-task {512, 2048, 8192} (and 8 or 16 entries per
+ * lane when k = 1) and keep the fastest.  Synchronises `stream`. */
+MAXE_API maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream);
+/* The handle's batch plan (any output may be NULL). */
+MAXE_API maxe_status maxe_batch_plan_info(const maxe_handle* h, int64_t* entries_per_task, int32_t* tasks,
+                                          int32_t* items_per_lane);
+
 /* Power iteration on a square handle, in the original space (v <- A v / ||A v||_2,
  * `steps` times from v0, then lambda = v^T A v).  Not in the paper: it is the
  * iterative reuse of the matrix that the paper's preconditioning analogy

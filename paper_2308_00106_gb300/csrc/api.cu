@@ -42,6 +42,7 @@ void release(maxe_handle* h) {
   if (!h) return;
   const Allocator& al = h->al;
   al.put(h->xbuf);
+  al.put(h->bwrow);
   al.put(h->wrow[1]);
   al.put(h->wrow[0]);
   al.put(h->cperm);
@@ -142,6 +143,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   h->status = di.status;
   maxe_status s = permute_csr_run(A, rperm, cperm, flags, h, st);
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
+  if (s == MAXE_OK) s = batch_plan_default(h, st);
   if (s == MAXE_OK && (flags & MAXE_ITEMS16)) h->spmv_items16 = 1;
   if (s == MAXE_OK && (flags & MAXE_AUTOTUNE)) s = spmv_autotune(h, st);
   if (s != MAXE_OK) {

@@ -1,0 +1,406 @@
+// batch.cu -- batched persistent SpMV/SpMM: many permuted matrices, each with
+// its own k right-hand sides, in one launch per value type.
+//
+// Each item is (handle, k, X, ldx, Y, ldy): Y = A' X with X in the permuted
+// space, Y written in the permuted space or, with MAXE_BATCH_SCATTER_Y,
+// through rperm into the original space.  Every handle carries a batch plan
+// (entries per warp task H_b and entries per lane), built once per handle
+// (default or tuned by maxe_batch_tune) and independent of what else is in a
+// batch, so a matrix gives the same bits alone and in any mix.
+//
+// The launch keeps (blocks per SM x SMs) blocks resident; every warp walks the
+// flat list of tasks (item, warp range) with a grid stride, runs each range
+// through the same per-warp TMA ring as the single-matrix kernel (the ring's
+// mbarrier phase count carries over between tasks), and picks the kernel
+// variant (VW columns per pass, 8 or 16 entries per lane) per item.  A batch
+// object stages its descriptor table in pinned host memory and uploads it on
+// the stream before the launch, so batch runs can be captured in a CUDA graph.
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "spmv_warp.cuh"
+
+namespace maxe {
+namespace {
+
+using namespace warp;
+
+struct BatchItem {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const void* val;
+  const void* X;
+  void* Y;
+  const int32_t* yperm;
+  const int32_t* wrow;
+  int64_t ldx, ldy;
+  int32_t k, M, nW, vw, it16, unit;
+};
+
+struct BatchParams {
+  const BatchItem* items;
+  const int32_t* task0;  // first task of each item, nitems + 1 entries
+  unsigned* status;
+  int32_t nitems, ntasks;
+};
+
+constexpr int kBatchMinBlocks = 2;
+
+template <typename VT>
+constexpr size_t batch_warp_smem() {
+  size_t m = sizeof(WarpSmem<VT, 1, 8>);
+  m = std::max(m, sizeof(WarpSmem<VT, 1, 16>));
+  m = std::max(m, sizeof(WarpSmem<VT, 2, 8>));
+  if (sizeof(typename Acc<VT>::T) == 4) m = std::max(m, sizeof(WarpSmem<VT, 4, 8>));
+  return (m + 127) & ~size_t(127);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads, kBatchMinBlocks) spmm_batch_kernel(BatchParams bp) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5;
+  unsigned char* wsmem = smem_raw + batch_warp_smem<VT>() * wib;
+  init_ring<Cfg<VT, 1, 8, true>>(wsmem);  // barriers sit at offset 0 in every variant
+  uint32_t gi = 0;
+  const int nwarps = gridDim.x * kWarps;
+  for (int t = blockIdx.x * kWarps + wib; t < bp.ntasks; t += nwarps) {
+    int lo = 0, hi = bp.nitems - 1;  // item of task t: last item with task0 <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bp.task0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const BatchItem& it = bp.items[lo];
+    Params p;
+    p.rowptr = it.rowptr;
+    p.col = it.col;
+    p.val = it.val;
+    p.X = it.X;
+    p.Y = it.Y;
+    p.yperm = it.yperm;
+    p.wrow = it.wrow;
+    p.status = bp.status;
+    p.ldx = it.ldx;
+    p.ldy = it.ldy;
+    p.k = it.k;
+    p.M = it.M;
+    p.nW = it.nW;
+    const int w = t - bp.task0[lo];
+    bool ok;
+    if (it.vw == 1) {
+      if (it.unit)
+        ok = it.it16 ? process_range<Cfg<VT, 1, 16, true>>(p, w, wsmem, gi)
+                     : process_range<Cfg<VT, 1, 8, true>>(p, w, wsmem, gi);
+      else
+        ok = process_range<Cfg<VT, 1, 8, false>>(p, w, wsmem, gi);
+    } else if (it.vw == 2) {
+      ok = process_range<Cfg<VT, 2, 8, false>>(p, w, wsmem, gi);
+    } else {
+      if constexpr (sizeof(typename Acc<VT>::T) == 4)
+        ok = process_range<Cfg<VT, 4, 8, false>>(p, w, wsmem, gi);
+      else
+        ok = false;
+    }
+    if (!ok) return;
+  }
+}
+
+template <typename VT>
+maxe_status batch_prepare(int* blocks_per_sm) {
+  static int occ = -1;
+  if (occ < 0) {
+    const size_t smem = batch_warp_smem<VT>() * kWarps;
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_batch_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem)));
+    int o = 0;
+    MAXE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_batch_kernel<VT>, kThreads, smem));
+    occ = o > 0 ? o : 1;
+  }
+  *blocks_per_sm = occ;
+  return MAXE_OK;
+}
+
+template <typename VT>
+maxe_status batch_launch(const BatchParams& bp, int sms, cudaStream_t st) {
+  int occ = 1;
+  MAXE_TRY(batch_prepare<VT>(&occ));
+  const int64_t want = ceil_div(bp.ntasks, kWarps);
+  const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * occ)));
+  spmm_batch_kernel<VT><<<grid, kThreads, batch_warp_smem<VT>() * kWarps, st>>>(bp);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  return MAXE_OK;
+}
+
+maxe_status launch_for(maxe_dtype d, const BatchParams& bp, int sms, cudaStream_t st) {
+  switch (d) {
+    case MAXE_F64: return batch_launch<double>(bp, sms, st);
+    case MAXE_F32: return batch_launch<float>(bp, sms, st);
+    case MAXE_BF16: return batch_launch<uint16_t>(bp, sms, st);
+  }
+  return MAXE_ERR_INVALID;
+}
+
+// resident warps of the batched kernel for one value type
+int batch_resident_warps(maxe_dtype d, int sms) {
+  int occ = 1;
+  maxe_status s = MAXE_OK;
+  switch (d) {
+    case MAXE_F64: s = batch_prepare<double>(&occ); break;
+    case MAXE_F32: s = batch_prepare<float>(&occ); break;
+    case MAXE_BF16: s = batch_prepare<uint16_t>(&occ); break;
+  }
+  if (s != MAXE_OK) occ = 1;
+  return sms * occ * kWarps;
+}
+
+int pick_vw(const maxe_batch_item& a, int eb) {
+  if (a.k == 1) return 1;
+  auto aligned = [&](int vw) {
+    const uintptr_t al = static_cast<uintptr_t>(vw) * eb;
+    return a.ldx % vw == 0 && a.ldy % vw == 0 && reinterpret_cast<uintptr_t>(a.X) % al == 0 &&
+           reinterpret_cast<uintptr_t>(a.Y) % al == 0;
+  };
+  if (eb == 4 && a.k >= 3 && aligned(4)) return 4;
+  if (aligned(2)) return 2;
+  return 1;
+}
+
+}  // namespace
+
+// Batch plan of a handle: a partition with H_b entries per warp task.
+maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st) {
+  H = std::max<int64_t>(256, H);
+  const int64_t nW = std::max<int64_t>(1, ceil_div(h->nnz, H));
+  int32_t* w = static_cast<int32_t*>(h->al.get(static_cast<size_t>(nW + 1) * sizeof(int32_t)));
+  if (!w) return MAXE_ERR_OOM;
+  maxe_status s = bucket_lower_bounds(h->rowptr, h->rows, H, 0, nW, w, st);
+  if (s == MAXE_OK) s = set_i32(w + nW, h->rows, st);
+  if (s != MAXE_OK) {
+    h->al.put(w);
+    return s;
+  }
+  h->al.put(h->bwrow);
+  h->bwrow = w;
+  h->bnW = static_cast<int32_t>(nW);
+  h->bH = H;
+  h->bit16 = it16;
+  return MAXE_OK;
+}
+
+maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st) {
+  const int64_t target = batch_resident_warps(h->dtype, h->sms);
+  return batch_plan(h, std::max<int64_t>(kDefaultBatchTask, ceil_div(std::max<int64_t>(h->nnz, 1), target)), 0, st);
+}
+
+}  // namespace maxe
+
+using namespace maxe;
+
+struct maxe_batch {
+  int32_t capacity = 0;
+  int32_t n = 0;
+  Allocator al;
+  int sms = 0;
+  unsigned* status = nullptr;
+  // per value type: host staging (pinned) and device tables
+  BatchItem* h_items = nullptr;
+  int32_t* h_task0 = nullptr;
+  BatchItem* d_items = nullptr;
+  int32_t* d_task0 = nullptr;
+  cudaEvent_t uploaded = nullptr;  // the last upload from the staging has executed
+  bool pending = false;
+  std::vector<maxe_batch_item> items;
+};
+
+namespace {
+
+void batch_release(maxe_batch* b) {
+  if (!b) return;
+  if (b->uploaded) {
+    cudaEventSynchronize(b->uploaded);
+    cudaEventDestroy(b->uploaded);
+  }
+  b->al.put(b->d_task0);
+  b->al.put(b->d_items);
+  if (b->h_task0) cudaFreeHost(b->h_task0);
+  if (b->h_items) cudaFreeHost(b->h_items);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+maxe_status maxe_batch_create(int32_t capacity, const maxe_allocator* alloc, void* stream, maxe_batch** out) {
+  if (!out || capacity < 1 || capacity > (1 << 20)) return MAXE_ERR_INVALID;
+  *out = nullptr;
+  DeviceInfo di{};
+  MAXE_TRY(device_info(&di));
+  cudaStream_t st = as_stream(stream);
+  maxe_batch* b = new (std::nothrow) maxe_batch();
+  if (!b) return MAXE_ERR_OOM;
+  b->capacity = capacity;
+  b->al = Allocator(alloc, st);
+  b->sms = di.sms;
+  b->status = di.status;
+  // one table slot per item plus a sentinel, for each of the 3 value types
+  const size_t ni = static_cast<size_t>(capacity) * 3, nt = static_cast<size_t>(capacity + 1) * 3;
+  if (cudaMallocHost(reinterpret_cast<void**>(&b->h_items), ni * sizeof(BatchItem)) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&b->h_task0), nt * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    batch_release(b);
+    return MAXE_ERR_OOM;
+  }
+  b->d_items = static_cast<BatchItem*>(b->al.get(ni * sizeof(BatchItem)));
+  b->d_task0 = static_cast<int32_t*>(b->al.get(nt * sizeof(int32_t)));
+  if (!b->d_items || !b->d_task0) {
+    batch_release(b);
+    return MAXE_ERR_OOM;
+  }
+  if (cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    b->uploaded = nullptr;
+    batch_release(b);
+    return MAXE_ERR_CUDA;
+  }
+  b->items.reserve(capacity);
+  *out = b;
+  return MAXE_OK;
+}
+
+maxe_status maxe_batch_set(maxe_batch* b, const maxe_batch_item* items, int32_t n) {
+  if (!b || n < 0 || n > b->capacity || (n > 0 && !items)) return MAXE_ERR_INVALID;
+  for (int32_t i = 0; i < n; ++i) {
+    const maxe_batch_item& a = items[i];
+    if (!a.h || a.k < 1 || a.k > 64 || a.ldx < a.k || a.ldy < a.k) return MAXE_ERR_INVALID;
+    if ((a.h->cols > 0 && !a.X) || (a.h->rows > 0 && !a.Y)) return MAXE_ERR_INVALID;
+    if (a.flags & ~static_cast<uint32_t>(MAXE_BATCH_SCATTER_Y)) return MAXE_ERR_INVALID;
+    if (!a.h->bwrow) return MAXE_ERR_INVALID;
+  }
+  b->items.assign(items, items + n);
+  b->n = n;
+  return MAXE_OK;
+}
+
+maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
+  if (!b) return MAXE_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  MAXE_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  // the staging is read by the previous run's copies when they execute: wait for them
+  if (b->pending && cap == cudaStreamCaptureStatusNone) {
+    MAXE_CUDA_TRY(cudaEventSynchronize(b->uploaded));
+    b->pending = false;
+  }
+  const maxe_dtype types[3] = {MAXE_F64, MAXE_F32, MAXE_BF16};
+  for (int ti = 0; ti < 3; ++ti) {
+    BatchItem* hi = b->h_items + static_cast<size_t>(ti) * b->capacity;
+    int32_t* ht = b->h_task0 + static_cast<size_t>(ti) * (b->capacity + 1);
+    int32_t m = 0;
+    int64_t tasks = 0;
+    for (const maxe_batch_item& a : b->items) {
+      const maxe_handle* h = a.h;
+      if (h->dtype != types[ti] || h->rows == 0) continue;
+      const int eb = vector_bytes(h->dtype);
+      BatchItem& d = hi[m];
+      d.rowptr = h->rowptr;
+      d.col = h->col;
+      d.val = h->val;
+      d.X = a.X;
+      d.Y = a.Y;
+      d.yperm = (a.flags & MAXE_BATCH_SCATTER_Y) ? h->rperm : nullptr;
+      d.wrow = h->bwrow;
+      d.ldx = a.ldx;
+      d.ldy = a.ldy;
+      d.k = a.k;
+      d.M = h->rows;
+      d.nW = h->bnW;
+      d.vw = pick_vw(a, eb);
+      d.unit = (a.k == 1 && a.ldx == 1 && a.ldy == 1) ? 1 : 0;
+      d.it16 = (d.unit && h->bit16) ? 1 : 0;
+      ht[m] = static_cast<int32_t>(tasks);
+      tasks += h->bnW;
+      ++m;
+    }
+    if (m == 0) continue;
+    if (tasks > INT32_MAX) return MAXE_ERR_UNSUPPORTED;
+    ht[m] = static_cast<int32_t>(tasks);
+    BatchItem* di = b->d_items + static_cast<size_t>(ti) * b->capacity;
+    int32_t* dt = b->d_task0 + static_cast<size_t>(ti) * (b->capacity + 1);
+    MAXE_CUDA_TRY(cudaMemcpyAsync(di, hi, sizeof(BatchItem) * m, cudaMemcpyHostToDevice, st));
+    MAXE_CUDA_TRY(cudaMemcpyAsync(dt, ht, sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, st));
+    BatchParams bp{di, dt, b->status, m, static_cast<int32_t>(tasks)};
+    MAXE_TRY(launch_for(types[ti], bp, b->sms, st));
+  }
+  if (cap == cudaStreamCaptureStatusNone) {
+    MAXE_CUDA_TRY(cudaEventRecord(b->uploaded, st));
+    b->pending = true;
+  }
+  return MAXE_OK;
+}
+
+maxe_status maxe_batch_destroy(maxe_batch* b) {
+  batch_release(b);
+  return MAXE_OK;
+}
+
+maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
+  if (!h || k < 1 || k > 64) return MAXE_ERR_INVALID;
+  if (h->rows == 0 || h->nnz == 0) return MAXE_OK;
+  cudaStream_t st = as_stream(stream);
+  const int eb = vector_bytes(h->dtype);
+  ScratchSet scratch(h->al);
+  void* X = scratch.get<unsigned char>(static_cast<size_t>(h->cols) * k * eb);
+  void* Y = scratch.get<unsigned char>(static_cast<size_t>(h->rows) * k * eb);
+  if (!X || !Y) return MAXE_ERR_OOM;
+  MAXE_CUDA_TRY(cudaMemsetAsync(X, 0, static_cast<size_t>(h->cols) * k * eb, st));
+  maxe_batch* b = nullptr;
+  MAXE_TRY(maxe_batch_create(1, nullptr, stream, &b));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  maxe_status s = (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) ? MAXE_OK
+                                                                                             : MAXE_ERR_CUDA;
+  const int64_t floor_h = ceil_div(h->nnz, batch_resident_warps(h->dtype, h->sms));
+  const int64_t cand_h[3] = {std::max<int64_t>(512, floor_h), std::max<int64_t>(2048, floor_h),
+                             std::max<int64_t>(8192, floor_h)};
+  float best = 1e30f;
+  int64_t best_h = cand_h[1];
+  int best_it = 0;
+  maxe_batch_item item{h, k, X, k, Y, k, 0u};
+  for (int ci = 0; ci < 3 && s == MAXE_OK; ++ci) {
+    for (int it16 = 0; it16 <= (k == 1 ? 1 : 0) && s == MAXE_OK; ++it16) {
+      s = batch_plan(h, cand_h[ci], it16, st);
+      if (s == MAXE_OK) s = maxe_batch_set(b, &item, 1);
+      for (int rep = 0; rep < 2 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
+      if (s != MAXE_OK) break;
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 5 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) s = MAXE_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (s == MAXE_OK && ms < best) {
+        best = ms;
+        best_h = cand_h[ci];
+        best_it = it16;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  maxe_batch_destroy(b);
+  if (s == MAXE_OK) s = batch_plan(h, best_h, best_it, st);
+  if (s == MAXE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = MAXE_ERR_CUDA;
+  return s;
+}
+
+maxe_status maxe_batch_plan_info(const maxe_handle* h, int64_t* entries_per_task, int32_t* tasks,
+                                 int32_t* items_per_lane) {
+  if (!h) return MAXE_ERR_INVALID;
+  if (entries_per_task) *entries_per_task = h->bH;
+  if (tasks) *tasks = h->bnW;
+  if (items_per_lane) *items_per_lane = h->bit16 ? 16 : 8;
+  return MAXE_OK;
+}
+
+}  // extern "C"

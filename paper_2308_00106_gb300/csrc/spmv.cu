@@ -28,357 +28,13 @@
 // SpMM: X rows are gathered VW columns at a time (float4 / float2 / double2),
 // and the scan runs on VW-wide vectors, one pass per group of VW columns.
 #include <algorithm>
-#include <climits>
 
-#include "handle.cuh"
+#include "spmv_warp.cuh"
 
 namespace maxe {
 namespace {
 
-constexpr int kWarps = 8;        // warps per block
-constexpr int kThreads = kWarps * 32;
-constexpr int kStages = 2;               // bulk-copy ring depth per warp
-constexpr int kMaxItems = 16;            // consecutive entries per lane: 8 or 16 (tuned per handle)
-constexpr int kMaxK = 64;
-
-template <typename VT>
-struct Acc;
-template <>
-struct Acc<double> {
-  using T = double;
-};
-template <>
-struct Acc<float> {
-  using T = float;
-};
-template <>
-struct Acc<uint16_t> {
-  using T = float;
-};
-
-struct Params {
-  const int32_t* rowptr;
-  const int32_t* col;
-  const void* val;
-  const void* X;
-  void* Y;
-  const int32_t* yperm;
-  const int32_t* wrow;
-  unsigned* status;
-  int64_t ldx, ldy;
-  int32_t k, M, nW;
-};
-
-template <int VW, typename AT>
-__device__ __forceinline__ void xload(const AT* __restrict__ X, int32_t c, int64_t ldx, int c0, int k, AT (&xv)[VW]) {
-  const AT* px = X + static_cast<int64_t>(c) * ldx + c0;
-  if constexpr (VW == 1) {
-    xv[0] = __ldg(px);
-  } else {
-    if (c0 + VW <= k) {
-      if constexpr (VW == 2 && sizeof(AT) == 4) {
-        const float2 u = __ldg(reinterpret_cast<const float2*>(px));
-        xv[0] = u.x, xv[1] = u.y;
-      } else if constexpr (VW == 2 && sizeof(AT) == 8) {
-        const double2 u = __ldg(reinterpret_cast<const double2*>(px));
-        xv[0] = u.x, xv[1] = u.y;
-      } else {
-        const float4 u = __ldg(reinterpret_cast<const float4*>(px));
-        xv[0] = u.x, xv[1] = u.y, xv[2] = u.z, xv[3] = u.w;
-      }
-    } else {
-#pragma unroll
-      for (int w = 0; w < VW; ++w) xv[w] = (c0 + w < k) ? __ldg(px + w) : AT(0);
-    }
-  }
-}
-
-template <int VW, typename AT>
-__device__ __forceinline__ void ystore(AT* __restrict__ Y, int64_t row, int64_t ldy, int c0, int k,
-                                       const AT (&v)[VW]) {
-  AT* py = Y + row * ldy + c0;
-  if constexpr (VW == 1) {
-    *py = v[0];
-  } else {
-    if (c0 + VW <= k) {
-      if constexpr (VW == 2 && sizeof(AT) == 4) {
-        *reinterpret_cast<float2*>(py) = make_float2(v[0], v[1]);
-      } else if constexpr (VW == 2 && sizeof(AT) == 8) {
-        *reinterpret_cast<double2*>(py) = make_double2(v[0], v[1]);
-      } else {
-        *reinterpret_cast<float4*>(py) = make_float4(v[0], v[1], v[2], v[3]);
-      }
-    } else {
-#pragma unroll
-      for (int w = 0; w < VW; ++w)
-        if (c0 + w < k) py[w] = v[w];
-    }
-  }
-}
-
-// Per-warp shared memory: an S-stage ring of COL/VAL pieces filled by 1-D bulk
-// copies (TMA) with one mbarrier per stage, the row-start bitmap of the current
-// piece, the scanned sums it is read back from, and the carries of the k columns.
-template <typename VT, int VW, int IT>
-struct alignas(16) WarpSmem {
-  using AT = typename Acc<VT>::T;
-  static constexpr int kPiece = 32 * IT;
-  int32_t col[kStages][kPiece];
-  VT val[kStages][kPiece];
-  AT sums[kPiece * VW];
-  uint32_t flags[kPiece / 32];
-  AT carry[kMaxK + 4];
-  uint64_t full[kStages];
-};
-
-template <typename VT, int VW, int IT>
-constexpr size_t block_smem() {
-  return sizeof(WarpSmem<VT, VW, IT>) * kWarps;
-}
-
-template <int IT>
-__device__ __forceinline__ void lds_vals(const float* p, float (&a)[IT]) {
-#pragma unroll
-  for (int i = 0; i < IT / 4; ++i) {
-    const float4 u = reinterpret_cast<const float4*>(p)[i];
-    a[4 * i] = u.x, a[4 * i + 1] = u.y, a[4 * i + 2] = u.z, a[4 * i + 3] = u.w;
-  }
-}
-template <int IT>
-__device__ __forceinline__ void lds_vals(const double* p, double (&a)[IT]) {
-#pragma unroll
-  for (int i = 0; i < IT / 2; ++i) {
-    const double2 u = reinterpret_cast<const double2*>(p)[i];
-    a[2 * i] = u.x, a[2 * i + 1] = u.y;
-  }
-}
-template <int IT>
-__device__ __forceinline__ void lds_vals(const uint16_t* p, float (&a)[IT]) {
-#pragma unroll
-  for (int i = 0; i < IT / 8; ++i) {
-    const uint4 u = reinterpret_cast<const uint4*>(p)[i];
-    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      a[8 * i + 2 * q] = __uint_as_float(w4[q] << 16);
-      a[8 * i + 2 * q + 1] = __uint_as_float(w4[q] & 0xFFFF0000u);
-    }
-  }
-}
-
-template <typename VT, int VW, int IT>
-__device__ __forceinline__ void issue_piece(WarpSmem<VT, VW, IT>& ws, int s, const Params& p, int32_t base,
-                                            uint64_t pol) {
-  constexpr int kPiece = 32 * IT;
-  mbar_arrive_expect_tx(&ws.full[s], kPiece * (4u + static_cast<uint32_t>(sizeof(VT))));
-  bulk_g2s(ws.col[s], p.col + base, kPiece * 4u, &ws.full[s], pol);
-  bulk_g2s(ws.val[s], static_cast<const VT*>(p.val) + base, kPiece * static_cast<uint32_t>(sizeof(VT)), &ws.full[s],
-           pol);
-}
-
-// One kernel variant: value type VT, VW columns per pass, IT entries per lane;
-// UNIT: k = 1 with unit strides (plain SpMV), so x and y are indexed directly.
-// kMinBlocks: resident blocks per SM the register budget is cut for.
-template <typename VT_, int VW_, int IT_, bool UNIT_>
-struct Cfg {
-  using VT = VT_;
-  static constexpr int VW = VW_, IT = IT_;
-  static constexpr bool UNIT = UNIT_;
-  static constexpr int kMinBlocks =
-      IT == 16 ? 2 : (sizeof(typename Acc<VT>::T) == 8 ? (VW == 1 ? 3 : 2) : (VW == 1 ? 4 : (VW == 2 ? 3 : 2)));
-};
-
-template <class C>
-__global__ void __launch_bounds__(kThreads, C::kMinBlocks) spmm_warp_kernel(Params p) {
-  using VT = typename C::VT;
-  constexpr int VW = C::VW, IT = C::IT;
-  constexpr bool UNIT = C::UNIT;
-  using AT = typename Acc<VT>::T;
-  constexpr int kItems = IT;
-  constexpr int kPiece = 32 * IT;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int w = blockIdx.x * kWarps + wib;
-  if (w >= p.nW) return;
-  WarpSmem<VT, VW, IT>& ws = reinterpret_cast<WarpSmem<VT, VW, IT>*>(smem_raw)[wib];
-  const AT* X = static_cast<const AT*>(p.X);
-  AT* Y = static_cast<AT*>(p.Y);
-  const int k = p.k;
-  const int ngroups = (k + VW - 1) / VW;
-
-  const int32_t r_hi = p.wrow[w + 1];
-  int32_t r = p.wrow[w];  // first row of the range not yet written
-  const int32_t e_lo = p.rowptr[r];
-  const int32_t e_hi = p.rowptr[r_hi];
-  const int32_t base0 = e_lo & ~7;  // 16-byte aligned for every value type
-  const int32_t npieces = (e_hi > base0) ? (e_hi - base0 + kPiece - 1) / kPiece : 0;
-  const uint64_t pol = policy_evict_first();
-  if (lane == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&ws.full[s], 1);
-    fence_mbar_init();
-  }
-  for (int c = lane; c < ngroups * VW; c += 32) ws.carry[c] = AT(0);
-  if (lane < kPiece / 32) ws.flags[lane] = 0u;
-  __syncwarp();
-  if (lane == 0)
-    for (int s = 0; s < kStages && s < npieces; ++s) issue_piece(ws, s, p, base0 + s * kPiece, pol);
-
-  int32_t r_start = e_lo;  // first entry of row r
-  int32_t end0 = (r + lane < r_hi) ? __ldg(p.rowptr + r + 1 + lane) : INT_MAX;
-
-  for (int32_t i = 0; i < npieces; ++i) {
-    const int s = i % kStages;
-    const int32_t base = base0 + i * kPiece;
-    // rows ending in this piece: flags in the bitmap, count, last end
-    int nend = 0;
-    int32_t last_o = -1;
-    {
-      int32_t end = end0;
-      while (true) {
-        const int32_t o = end - base;  // end <= INT_MAX and base >= 0: no overflow
-        const bool in = o <= kPiece;
-        const int n = __popc(__ballot_sync(0xffffffffu, in));
-        if (in && o >= 1 && o < kPiece) atomicOr(&ws.flags[o >> 5], 1u << (o & 31));
-        if (n > 0) last_o = __shfl_sync(0xffffffffu, o, n - 1);
-        nend += n;
-        if (n < 32) break;
-        const int32_t rr = r + nend + lane;
-        end = (rr < r_hi) ? __ldg(p.rowptr + rr + 1) : INT_MAX;
-      }
-    }
-    const int32_t rn = r + nend;
-    const int32_t end_first = end0;
-    end0 = (rn + lane < r_hi) ? __ldg(p.rowptr + rn + 1 + lane) : INT_MAX;  // next piece, one step ahead
-    __syncwarp();
-    const uint32_t fw = (ws.flags[(kItems * lane) >> 5] >> ((kItems * lane) & 31)) & ((1u << kItems) - 1u);
-    const int first_flag = fw ? __ffs(fw) - 1 : kItems;
-
-    bool ok = mbar_wait_bounded(&ws.full[s], static_cast<uint32_t>((i / kStages) & 1), p.status);
-    if (!__all_sync(0xffffffffu, ok)) return;
-    int32_t cj[kItems];
-    AT a[kItems];
-#pragma unroll
-    for (int q = 0; q < kItems / 4; ++q) {
-      const int4 u = reinterpret_cast<const int4*>(ws.col[s] + kItems * lane)[q];
-      cj[4 * q] = u.x, cj[4 * q + 1] = u.y, cj[4 * q + 2] = u.z, cj[4 * q + 3] = u.w;
-    }
-    lds_vals<IT>(ws.val[s] + kItems * lane, a);
-    __syncwarp();
-    if (lane < kPiece / 32) ws.flags[lane] = 0u;  // every lane has its flag bits
-    // entries outside [e_lo, e_hi) belong to other warps (first and last piece only)
-    uint32_t vmask = (1u << kItems) - 1u;
-    if (!(base >= e_lo && base + kPiece <= e_hi)) {
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        const int32_t e = base + kItems * lane + j;
-        if (e < e_lo || e >= e_hi) vmask &= ~(1u << j);
-      }
-    }
-    // the stage is in registers: refill it with piece i + kStages
-    __syncwarp();
-    if (lane == 0 && i + kStages < npieces) {
-      fence_proxy_async_smem();
-      issue_piece(ws, s, p, base + kStages * kPiece, pol);
-    }
-
-    for (int g = 0; g < ngroups; ++g) {
-      const int c0 = g * VW;
-      AT v[kItems][VW];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j) {
-        if ((vmask >> j) & 1u) {
-          AT xv[VW];
-          if constexpr (UNIT) {
-            xv[0] = X[cj[j]];  // plain load: read-only-path loads here trip ptxas (C7600)
-          } else {
-            xload<VW>(X, cj[j], p.ldx, c0, k, xv);
-          }
-#pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] = a[j] * xv[u];
-        } else {
-#pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] = AT(0);
-        }
-      }
-#pragma unroll
-      for (int j = 1; j < kItems; ++j)
-        if (!((fw >> j) & 1u))
-#pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] += v[j - 1][u];
-      int F = fw != 0u;
-      AT V[VW];
-#pragma unroll
-      for (int u = 0; u < VW; ++u) V[u] = v[kItems - 1][u];
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int Fu = __shfl_up_sync(0xffffffffu, F, d);
-        AT Vu[VW];
-#pragma unroll
-        for (int u = 0; u < VW; ++u) Vu[u] = __shfl_up_sync(0xffffffffu, V[u], d);
-        if (lane >= d) {
-          if (!F)
-#pragma unroll
-            for (int u = 0; u < VW; ++u) V[u] += Vu[u];
-          F |= Fu;
-        }
-      }
-      const int Fe = __shfl_up_sync(0xffffffffu, F, 1);
-      AT P[VW];
-#pragma unroll
-      for (int u = 0; u < VW; ++u) {
-        const AT Ve = __shfl_up_sync(0xffffffffu, V[u], 1);
-        const AT cin = ws.carry[c0 + u];
-        P[u] = (lane == 0) ? cin : (Fe ? Ve : cin + Ve);
-      }
-#pragma unroll
-      for (int j = 0; j < kItems; ++j)
-        if (j < first_flag)
-#pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] += P[u];
-#pragma unroll
-      for (int j = 0; j < kItems; ++j)
-#pragma unroll
-        for (int u = 0; u < VW; ++u) ws.sums[(kItems * lane + j) * VW + u] = v[j][u];
-      __syncwarp();
-      // rows that end in the piece
-      int32_t prev_end = r_start;
-      for (int b = 0; b < nend; b += 32) {
-        const int32_t rr = r + b + lane;
-        int32_t end = end_first;
-        if (b > 0) end = (rr < r_hi) ? __ldg(p.rowptr + rr + 1) : INT_MAX;
-        int32_t start = __shfl_up_sync(0xffffffffu, end, 1);
-        if (lane == 0) start = prev_end;
-        if (b + lane < nend) {
-          AT out[VW];
-          if (end > start) {
-            const AT* src = ws.sums + (end - base - 1) * VW;
-#pragma unroll
-            for (int u = 0; u < VW; ++u) out[u] = src[u];
-          } else {
-#pragma unroll
-            for (int u = 0; u < VW; ++u) out[u] = AT(0);
-          }
-          const int32_t row = p.yperm ? p.yperm[rr] : rr;
-          if constexpr (UNIT)
-            Y[row] = out[0];
-          else
-            ystore<VW>(Y, static_cast<int64_t>(row), p.ldy, c0, k, out);
-        }
-        prev_end = __shfl_sync(0xffffffffu, end, 31);
-      }
-      // partial row running on into the next piece
-      if (lane < VW) ws.carry[c0 + lane] = (last_o == kPiece) ? AT(0) : ws.sums[(kPiece - 1) * VW + lane];
-      __syncwarp();
-    }
-    if (nend > 0) r_start = base + last_o;
-    r = rn;
-  }
-  // rows left over are empty (their entries were all consumed)
-  for (int32_t rr = r + lane; rr < r_hi; rr += 32) {
-    const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
-    for (int c = 0; c < k; ++c) Y[row * p.ldy + c] = AT(0);
-  }
-}
+using namespace warp;
 
 template <typename VT, int VW, int IT, bool UNIT>
 maxe_status prepare_variant() {

@@ -34,7 +34,10 @@ EXPORTS = [
     "maxe_build_permutation", "maxe_invert_permutation", "maxe_permute_gather", "maxe_permute_scatter",
     "maxe_permute_csr", "maxe_handle_csr", "maxe_handle_tuning", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmm", "maxe_power_iteration",
     "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
+    "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
+    "maxe_batch_plan_info",
 ]
+MAXE_BATCH_SCATTER_Y = 0x1
 
 
 class MaxeError(RuntimeError):
@@ -47,6 +50,11 @@ class _Allocator(ctypes.Structure):
     _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)),
                 ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)),
                 ("ctx", ctypes.c_void_p)]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("k", ctypes.c_int32), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64),
+                ("Y", ctypes.c_void_p), ("ldy", ctypes.c_int64), ("flags", ctypes.c_uint32)]
 
 
 class _Csr(ctypes.Structure):
@@ -109,6 +117,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_power_iteration": [P, P, I32, P, ctypes.POINTER(ctypes.c_double), P],
             "maxe_handle_destroy": [P],
             "maxe_device_status": [P],
+            "maxe_batch_create": [I32, P, P, ctypes.POINTER(P)],
+            "maxe_batch_set": [P, ctypes.POINTER(_BatchItem), I32],
+            "maxe_batch_run": [P, P],
+            "maxe_batch_destroy": [P],
+            "maxe_batch_tune": [P, I32, P],
+            "maxe_batch_plan_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -333,3 +347,61 @@ def maxe_version() -> str:
 def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
     return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16)
+
+
+class Batch:
+    """Batched persistent SpMV/SpMM over many handles (maxe_batch_*).
+
+    items: list of (handle, X, Y, scatter_y) with X (cols x k) in the permuted
+    space and Y (rows x k) written in the permuted space, or through rperm when
+    scatter_y is True.  Tensors must stay alive while the batch may run."""
+
+    def __init__(self, capacity: int, stream=None):
+        out = ctypes.c_void_p()
+        _check(load().maxe_batch_create(capacity, ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)),
+                                        ctypes.byref(out)), "maxe_batch_create")
+        self.ptr = out.value
+        self._keep = []
+
+    def set(self, items):
+        arr = (_BatchItem * max(len(items), 1))()
+        keep = []
+        for i, (h, X, Y, scatter) in enumerate(items):
+            if X.dim() == 1:
+                X = X.view(-1, 1)
+            if Y.dim() == 1:
+                Y = Y.view(-1, 1)
+            k = X.shape[1]
+            if X.dtype != h.vec_dtype or Y.dtype != h.vec_dtype or Y.shape[1] != k:
+                raise TypeError("batch item vectors do not match the handle")
+            arr[i] = _BatchItem(h.ptr, k, X.data_ptr(), X.stride(0), Y.data_ptr(), Y.stride(0),
+                                MAXE_BATCH_SCATTER_Y if scatter else 0)
+            keep += [h, X, Y]
+        _check(load().maxe_batch_set(ctypes.c_void_p(self.ptr), arr, len(items)), "maxe_batch_set")
+        self._keep = keep
+
+    def run(self, stream=None):
+        _check(load().maxe_batch_run(ctypes.c_void_p(self.ptr), ctypes.c_void_p(_stream(stream))), "maxe_batch_run")
+
+    def close(self):
+        if self.ptr:
+            load().maxe_batch_destroy(ctypes.c_void_p(self.ptr))
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def maxe_batch_tune(h: Handle, k: int, stream=None):
+    _check(load().maxe_batch_tune(ctypes.c_void_p(h.ptr), k, ctypes.c_void_p(_stream(stream))), "maxe_batch_tune")
+
+
+def maxe_batch_plan_info(h: Handle):
+    """(entries per warp task, tasks, entries per lane) of the handle's batch plan."""
+    H, t, it = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().maxe_batch_plan_info(ctypes.c_void_p(h.ptr), ctypes.byref(H), ctypes.byref(t), ctypes.byref(it)),
+           "maxe_batch_plan_info")
+    return H.value, t.value, it.value
