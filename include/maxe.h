@@ -243,6 +243,21 @@ MAXE_API maxe_status maxe_batch_plan_info(const maxe_handle* h, int64_t* entries
 MAXE_API maxe_status maxe_power_iteration(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
                                  double* lambda_host, void* stream);
 
+/* Vector steps of a batched power iteration kept in the permuted space (used
+ * by the serving loop; not in the paper).  With Q = rinv[cperm] (so that
+ * u_next = P_c^{-1} P_r^{-1} w for w = A' u), square matrices only:
+ *   maxe_vec_norm_gather: nrm2 = sum w[i]^2 (FP64), u[j] = w[Q[j]] / sqrt(nrm2);
+ *   maxe_vec_dot_gather:  *out = sum_j u[j] * w[Q[j]] (FP64; the Rayleigh
+ *                         quotient v^T A v of the original-space iterate).
+ * Q: (device) int32[n] or NULL for the identity; w, u: (device) n elements of
+ * elem_bytes (4 = FP32, 8 = FP64); scratch: (device) >= 514 doubles, caller
+ * owned; out: (device) one double.  The reductions use a fixed split of the
+ * vector, so results are deterministic.  u and w must not overlap. */
+MAXE_API maxe_status maxe_vec_norm_gather(const int32_t* Q, int32_t n, int32_t elem_bytes, const void* w, void* u,
+                                          double* scratch, void* stream);
+MAXE_API maxe_status maxe_vec_dot_gather(const int32_t* Q, int32_t n, int32_t elem_bytes, const void* u,
+                                         const void* w, double* scratch, double* out, void* stream);
+
 /* Release a handle and everything it owns (through its allocator, on the
  * stream given at creation).  NULL is accepted. */
 MAXE_API maxe_status maxe_handle_destroy(maxe_handle* h);

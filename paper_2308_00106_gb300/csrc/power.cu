@@ -54,6 +54,39 @@ __global__ void scale_by_inv_norm(const T* __restrict__ w, const double* __restr
   v[i] = static_cast<T>(static_cast<double>(w[i]) * inv);
 }
 
+// out[j] = w[Q[j]] * (1 / sqrt(*nrm2))
+template <typename T>
+__global__ void gather_scale(const int32_t* __restrict__ Q, const T* __restrict__ w, const double* __restrict__ nrm2,
+                             int64_t n, T* __restrict__ out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double inv = 1.0 / sqrt(*nrm2);
+  const int64_t src = Q ? static_cast<int64_t>(Q[i]) : i;
+  out[i] = static_cast<T>(static_cast<double>(w[src]) * inv);
+}
+
+// part[b] = sum over block b's slice of u[i] * w[Q[i]]
+template <typename T>
+__global__ void __launch_bounds__(kDotThreads) dot_gather_partial(const T* __restrict__ u, const T* __restrict__ w,
+                                                                  const int32_t* __restrict__ Q, int64_t n,
+                                                                  double* __restrict__ part) {
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * per, hi = std::min<int64_t>(n, lo + per);
+  double acc = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kDotThreads)
+    acc += static_cast<double>(u[i]) * static_cast<double>(w[Q ? static_cast<int64_t>(Q[i]) : i]);
+  __shared__ double ws[kDotThreads / 32];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kDotThreads / 32; ++k) t += ws[k];
+    part[blockIdx.x] = t;
+  }
+}
+
 template <typename T>
 maxe_status dot(const T* a, const T* b, int64_t n, double* part, double* out, cudaStream_t st) {
   const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kDotBlocks, ceil_div(n, 4 * kDotThreads))));
@@ -96,6 +129,31 @@ maxe_status run(const maxe_handle* h, const T* v0, int32_t steps, T* v, double* 
   return MAXE_OK;
 }
 
+int dot_blocks(int64_t n) {
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kDotBlocks, ceil_div(n, 4 * kDotThreads))));
+}
+
+template <typename T>
+maxe_status norm_gather(const int32_t* Q, int64_t n, const T* w, T* u, double* scratch, cudaStream_t st) {
+  const int nb = dot_blocks(n);
+  dot_partial<T><<<nb, kDotThreads, 0, st>>>(w, w, n, scratch);
+  dot_final<<<1, 32, 0, st>>>(scratch, nb, scratch + kDotBlocks);
+  gather_scale<T><<<static_cast<unsigned>(std::max<int64_t>(1, ceil_div(n, 256))), 256, 0, st>>>(
+      Q, w, scratch + kDotBlocks, n, u);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  return MAXE_OK;
+}
+
+template <typename T>
+maxe_status dot_gather(const int32_t* Q, int64_t n, const T* u, const T* w, double* scratch, double* out,
+                       cudaStream_t st) {
+  const int nb = dot_blocks(n);
+  dot_gather_partial<T><<<nb, kDotThreads, 0, st>>>(u, w, Q, n, scratch);
+  dot_final<<<1, 32, 0, st>>>(scratch, nb, out);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  return MAXE_OK;
+}
+
 }  // namespace
 
 maxe_status power_iteration_run(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
@@ -106,3 +164,33 @@ maxe_status power_iteration_run(const maxe_handle* h, const void* v0, int32_t st
 }
 
 }  // namespace maxe
+
+extern "C" {
+
+maxe_status maxe_vec_norm_gather(const int32_t* Q, int32_t n, int32_t elem_bytes, const void* w, void* u,
+                                 double* scratch, void* stream) {
+  using namespace maxe;
+  if (n < 0 || (elem_bytes != 4 && elem_bytes != 8) || (n > 0 && (!w || !u || !scratch))) return MAXE_ERR_INVALID;
+  if (n == 0) return MAXE_OK;
+  cudaStream_t st = as_stream(stream);
+  if (elem_bytes == 8)
+    return norm_gather(Q, n, static_cast<const double*>(w), static_cast<double*>(u), scratch, st);
+  return norm_gather(Q, n, static_cast<const float*>(w), static_cast<float*>(u), scratch, st);
+}
+
+maxe_status maxe_vec_dot_gather(const int32_t* Q, int32_t n, int32_t elem_bytes, const void* u, const void* w,
+                                double* scratch, double* out, void* stream) {
+  using namespace maxe;
+  if (n < 0 || (elem_bytes != 4 && elem_bytes != 8) || !out || (n > 0 && (!w || !u || !scratch)))
+    return MAXE_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  if (n == 0) {
+    MAXE_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double), st));
+    return MAXE_OK;
+  }
+  if (elem_bytes == 8)
+    return dot_gather(Q, n, static_cast<const double*>(u), static_cast<const double*>(w), scratch, out, st);
+  return dot_gather(Q, n, static_cast<const float*>(u), static_cast<const float*>(w), scratch, out, st);
+}
+
+}  // extern "C"

@@ -35,7 +35,7 @@ EXPORTS = [
     "maxe_permute_csr", "maxe_handle_csr", "maxe_handle_tuning", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmm", "maxe_power_iteration",
     "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
     "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
-    "maxe_batch_plan_info",
+    "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather",
 ]
 MAXE_BATCH_SCATTER_Y = 0x1
 
@@ -123,6 +123,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_batch_destroy": [P],
             "maxe_batch_tune": [P, I32, P],
             "maxe_batch_plan_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32)],
+            "maxe_vec_norm_gather": [P, I32, I32, P, P, P, P],
+            "maxe_vec_dot_gather": [P, I32, I32, P, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -405,3 +407,16 @@ def maxe_batch_plan_info(h: Handle):
     _check(load().maxe_batch_plan_info(ctypes.c_void_p(h.ptr), ctypes.byref(H), ctypes.byref(t), ctypes.byref(it)),
            "maxe_batch_plan_info")
     return H.value, t.value, it.value
+
+
+def maxe_vec_norm_gather(Q: torch.Tensor | None, w: torch.Tensor, u: torch.Tensor, scratch: torch.Tensor, stream=None):
+    """u[j] = w[Q[j]] / ||w||_2 (FP64 norm); scratch: >= 514 float64 on the device."""
+    _check(load().maxe_vec_norm_gather(_ptr(Q), w.numel(), w.element_size(), _ptr(w), _ptr(u), _ptr(scratch),
+                                       ctypes.c_void_p(_stream(stream))), "maxe_vec_norm_gather")
+
+
+def maxe_vec_dot_gather(Q: torch.Tensor | None, u: torch.Tensor, w: torch.Tensor, scratch: torch.Tensor,
+                        out: torch.Tensor, stream=None):
+    """out[0] = sum_j u[j] * w[Q[j]] (FP64)."""
+    _check(load().maxe_vec_dot_gather(_ptr(Q), u.numel(), u.element_size(), _ptr(u), _ptr(w), _ptr(scratch),
+                                      _ptr(out), ctypes.c_void_p(_stream(stream))), "maxe_vec_dot_gather")
