@@ -279,7 +279,7 @@ def run_batched(args):
     rank, world, local = dist_setup(args)
     maxe.load(build_if_missing=(rank == 0))
     t0 = time.perf_counter()
-    mats, ks = W.batched_set(args.seed, device="cuda")
+    mats, ks = W.batched_set(args.seed, count=args.batch_count, device="cuda")
     t_gen = time.perf_counter() - t0
     hs, Xs, Ys, Yp = [], [], [], []
     t0 = time.perf_counter()
@@ -287,11 +287,15 @@ def run_batched(args):
         r = maxe.maxe_build_permutation(args.seed + m, A.rows, 0)
         c = maxe.maxe_build_permutation(args.seed + m, A.cols, 1)
         h = maxe.from_csr(A, r, c)
-        maxe.maxe_batch_tune(h, k)
+        if not (args.profile or args.no_tune):
+            maxe.maxe_batch_tune(h, k)
         hs.append(h)
-        Xs.append(W.matrix_rhs(m, A.cols, k, "f32", "cuda"))
-        Ys.append(torch.empty(A.rows, k, device="cuda"))
-        Yp.append(torch.empty(A.rows, k, device="cuda"))
+        kp = (k + 3) // 4 * 4  # leading dimension padded to 4 columns: 16-byte rows
+        Xb = torch.zeros(A.cols, kp, device="cuda")
+        Xb[:, :k] = W.matrix_rhs(m, A.cols, k, "f32", "cuda")
+        Xs.append(Xb[:, :k])
+        Ys.append(torch.empty(A.rows, kp, device="cuda")[:, :k])
+        Yp.append(torch.empty(A.rows, kp, device="cuda")[:, :k])
     torch.cuda.synchronize()
     t_prep = time.perf_counter() - t0
     total = sum(alg_bytes(A.rows, A.cols, A.nnz, 4, 4, 4, k) for A, k in zip(mats, ks))
@@ -305,6 +309,13 @@ def run_batched(args):
         for h, X, Y in zip(hs, Xs, Yp):
             maxe.maxe_spmm(h, X, Y, permuted=True)
 
+    if args.profile:
+        for _ in range(3):
+            step_batched()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "done", "matrices": len(mats)}))
+        return
+
     K = max(1, args.steps // 100)
     clocks = Clocks(local)
     clocks.start()
@@ -317,7 +328,7 @@ def run_batched(args):
     for m in range(min(8, len(mats))):
         nrp, ncol, nval, _, _ = hs[m].csr()
         ref = oracle.spmm(mats[m].rows, nrp.cpu().numpy(), ncol.cpu().numpy(), nval.cpu().numpy(), 1,
-                          Xs[m].cpu().double().numpy())
+                          Xs[m].cpu().double().numpy().copy())
         errs.append(float(np.linalg.norm(Ys[m].cpu().double().numpy() - ref) / np.linalg.norm(ref)))
     plans = [maxe.maxe_batch_plan_info(h) for h in hs]
     hbm, src = peaks()
@@ -370,6 +381,12 @@ def run_serving(args):
     for f in (0.5, 0.8, 0.95):
         loads[str(f)] = srv.run(serve.make_trace(n, len(mats), f * sat["req_per_s"], seed=3 + int(f * 100)))
     clk = clocks.stop()
+    # the same server without batching (one request per step), same traces
+    unb_sat = srv.run(serve.make_trace(n, len(mats), math.inf, seed=2), max_items=1)
+    unb_loads = {}
+    for f in (0.5, 0.8):
+        unb_loads[str(f)] = srv.run(serve.make_trace(n, len(mats), f * sat["req_per_s"], seed=3 + int(f * 100)),
+                                    max_items=1)
     # the same saturation trace served one request at a time with single-matrix launches
     trace = serve.make_trace(n, len(mats), math.inf, seed=2)
     torch.cuda.synchronize()
@@ -388,8 +405,10 @@ def run_serving(args):
             maxe.maxe_spmv(h, u, w, permuted=True)
             maxe.maxe_vec_dot_gather(srv.Q[r.mat], u, w, scratch, lam)
         else:
-            X = torch.rand(A.cols, r.k, device="cuda") * 2 - 1
-            maxe.maxe_spmm(h, X, permuted=True)
+            kp = (r.k + 3) // 4 * 4  # same padded layout as the server's buffers
+            X = torch.rand(A.cols, kp, device="cuda") * 2 - 1
+            Y = torch.empty(A.rows, kp, device="cuda")
+            maxe.maxe_spmm(h, X[:, :r.k], Y[:, :r.k], permuted=True)
         bytes_seq += srv.unit_bytes(r) * r.units
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
@@ -404,8 +423,14 @@ def run_serving(args):
                    "requests_per_trace": n, "resident_bytes": srv.resident_bytes,
                    "total_nnz": int(sum(A.nnz for A in mats))},
         "saturation": sat, "loads": loads,
-        "one_request_at_a_time": {"req_per_s": n / t_seq, "gbs": bytes_seq / t_seq / 1e9},
-        "throughput_vs_one_at_a_time": round(sat["req_per_s"] / (n / t_seq), 3),
+        "unbatched_server": {"saturation": {k: unb_sat[k] for k in ("req_per_s", "gbs", "p50_ms", "p99_ms")},
+                             "loads": {f: {k: v[k] for k in ("req_per_s", "gbs", "p50_ms", "p99_ms")}
+                                       for f, v in unb_loads.items()}},
+        "throughput_vs_unbatched_server": round(sat["req_per_s"] / unb_sat["req_per_s"], 3),
+        "one_request_at_a_time_bare_launches": {"req_per_s": n / t_seq, "gbs": bytes_seq / t_seq / 1e9,
+                                                "what": "requests launched back to back with no scheduler, "
+                                                        "no arrivals and no latency accounting"},
+        "throughput_vs_bare_launches": round(sat["req_per_s"] / (n / t_seq), 3),
         "roofline": {"bound": "hbm", "achieved": round(sat["gbs"], 3), "peak": hbm, "unit": "GB/s",
                      "frac": round(sat["gbs"] / hbm, 4), "peak_source": src},
         "gen_s": t_gen, "load_and_tune_s": t_load, "clocks": clk,
@@ -424,6 +449,8 @@ def main():
     ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag", "batched", "serving"],
                     default="powerlaw")
     ap.add_argument("--requests", type=int, default=1500, help="requests per serving trace")
+    ap.add_argument("--batch-count", type=int, default=256, help="matrices of the batched workload")
+    ap.add_argument("--no-tune", action="store_true", help="batched workload: default batch plans, no autotuning")
     ap.add_argument("--seed", type=int, default=2308)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -458,9 +485,9 @@ def main():
     rperm = maxe.maxe_build_permutation(args.seed, M, 0)
     cperm = maxe.maxe_build_permutation(args.seed, N, 1)
     ev[1].record()
-    hP = maxe.from_csr(A, rperm, cperm, autotune=True)
+    hP = maxe.from_csr(A, rperm, cperm, autotune=not args.profile)
     ev[2].record()
-    hN = maxe.from_csr(A, autotune=True)
+    hN = maxe.from_csr(A, autotune=not args.profile)
     ev[3].record()
     torch.cuda.synchronize()
     t_perm, t_pcsr = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])

@@ -185,12 +185,16 @@ MAXE_API maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uin
 /* a7.  Y = A X for k right-hand sides (1 <= k <= 64).  X: (device) row-major
  * cols x k with leading dimension ldx >= k; Y: (device) row-major rows x k,
  * ldy >= k.  Element type and flags as for maxe_spmv.  Without
- * MAXE_VEC_PERMUTED, rows of X are gathered into handle-owned scratch. */
+ * MAXE_VEC_PERMUTED, rows of X are gathered into handle-owned scratch.
+ * Speed: with 16-byte aligned X and Y and ldx, ldy multiples of 4 (FP32) or 2
+ * (FP64), rows are gathered 4 (2) columns per load, also when k is not a
+ * multiple (the padding columns of X are read and ignored; Y's are untouched). */
 MAXE_API maxe_status maxe_spmm(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y,
                       int64_t ldy, uint32_t flags, void* stream);
 
 /* a9.  Batched persistent SpMV/SpMM (many uneven matrices, each with its own
- * k right-hand sides, in one launch per value type present).
+ * k right-hand sides, in one persistent launch per value type and kernel
+ * class present: unit-stride SpMV with 8 or with 16 entries per lane, or SpMM).
  *
  * An item asks for Y = A' X on a handle: X (device) is in the permuted space
  * (x' = x[cperm], rows of X gathered), row-major cols x k with leading
@@ -227,9 +231,10 @@ MAXE_API maxe_status maxe_batch_set(maxe_batch* b, const maxe_batch_item* items,
 /* Upload the table and launch the persistent kernel(s) on `stream`. */
 MAXE_API maxe_status maxe_batch_run(maxe_batch* b, void* stream);
 MAXE_API maxe_status maxe_batch_destroy(maxe_batch* b);
-/* Autotune the handle's batch plan for k right-hand sides: time single-item
- * batches over entries-per-task {512, 2048, 8192} (and 8 or 16 entries per
- * lane when k = 1) and keep the fastest.  Synchronises `stream`. */
+/* Autotune the handle's batch plan for k right-hand sides: for entries per
+ * task in {512, 2048, 8192, 32768} (and 8 or 16 entries per lane when k = 1)
+ * time batches of copies of the item that fill the GPU several times over,
+ * and keep the plan with the best throughput.  Synchronises `stream`. */
 MAXE_API maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream);
 /* The handle's batch plan (any output may be NULL). */
 MAXE_API maxe_status maxe_batch_plan_info(const maxe_handle* h, int64_t* entries_per_task, int32_t* tasks,

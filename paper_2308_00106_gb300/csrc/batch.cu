@@ -1,5 +1,6 @@
 // batch.cu -- batched persistent SpMV/SpMM: many permuted matrices, each with
-// its own k right-hand sides, in one launch per value type.
+// its own k right-hand sides, in one persistent launch per value type and
+// kernel class present.
 //
 // Each item is (handle, k, X, ldx, Y, ldy): Y = A' X with X in the permuted
 // space, Y written in the permuted space or, with MAXE_BATCH_SCATTER_Y,
@@ -8,8 +9,9 @@
 // (default or tuned by maxe_batch_tune) and independent of what else is in a
 // batch, so a matrix gives the same bits alone and in any mix.
 //
-// The launch keeps (blocks per SM x SMs) blocks resident; every warp walks the
-// flat list of tasks (item, warp range) with a grid stride, runs each range
+// The launch keeps (blocks per SM x SMs) blocks resident; every warp takes
+// tasks (item, warp range) from a flat list (first by position, then from an
+// atomic counter, so uneven tasks balance out), runs each range
 // through the same per-warp TMA ring as the single-matrix kernel (the ring's
 // mbarrier phase count carries over between tasks), and picks the kernel
 // variant (VW columns per pass, 8 or 16 entries per lane) per item.  A batch
@@ -43,29 +45,42 @@ struct BatchParams {
   const BatchItem* items;
   const int32_t* task0;  // first task of each item, nitems + 1 entries
   unsigned* status;
+  int32_t* next;         // dynamic task counter (zeroed before the launch)
   int32_t nitems, ntasks;
 };
 
-constexpr int kBatchMinBlocks = 2;
+// Kernel classes: register budgets differ a lot between the variants, so each
+// class is its own persistent kernel (one launch per value type and class
+// present in a batch): 0 = plain SpMV (k = 1, unit strides), 8 entries per
+// lane; 1 = the same with 16 entries per lane; 2 = SpMM (1, 2 or 4 columns per
+// pass, any strides).
+constexpr int kClasses = 3;
 
-template <typename VT>
-constexpr size_t batch_warp_smem() {
-  size_t m = sizeof(WarpSmem<VT, 1, 8>);
-  m = std::max(m, sizeof(WarpSmem<VT, 1, 16>));
-  m = std::max(m, sizeof(WarpSmem<VT, 2, 8>));
-  if (sizeof(typename Acc<VT>::T) == 4) m = std::max(m, sizeof(WarpSmem<VT, 4, 8>));
-  return (m + 127) & ~size_t(127);
-}
+template <typename VT, int CLASS>
+struct BatchClass {
+  static constexpr int kMinBlocks = CLASS == 0 ? (sizeof(typename Acc<VT>::T) == 8 ? 3 : 4) : 2;
+  static constexpr size_t warp_smem() {
+    size_t m = 0;
+    if (CLASS == 0) m = sizeof(WarpSmem<VT, 1, 8>);
+    if (CLASS == 1) m = sizeof(WarpSmem<VT, 1, 16>);
+    if (CLASS == 2) {
+      m = std::max(sizeof(WarpSmem<VT, 1, 8>), sizeof(WarpSmem<VT, 2, 8>));
+      if (sizeof(typename Acc<VT>::T) == 4) m = std::max(m, sizeof(WarpSmem<VT, 4, 8>));
+    }
+    return (m + 127) & ~size_t(127);
+  }
+};
 
-template <typename VT>
-__global__ void __launch_bounds__(kThreads, kBatchMinBlocks) spmm_batch_kernel(BatchParams bp) {
+template <typename VT, int CLASS>
+__global__ void __launch_bounds__(kThreads, BatchClass<VT, CLASS>::kMinBlocks) spmm_batch_kernel(BatchParams bp) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5;
-  unsigned char* wsmem = smem_raw + batch_warp_smem<VT>() * wib;
+  unsigned char* wsmem = smem_raw + BatchClass<VT, CLASS>::warp_smem() * wib;
   init_ring<Cfg<VT, 1, 8, true>>(wsmem);  // barriers sit at offset 0 in every variant
   uint32_t gi = 0;
   const int nwarps = gridDim.x * kWarps;
-  for (int t = blockIdx.x * kWarps + wib; t < bp.ntasks; t += nwarps) {
+  // first task by position, then the next unclaimed one (tasks differ in cost)
+  for (int t = blockIdx.x * kWarps + wib; t < bp.ntasks;) {
     int lo = 0, hi = bp.nitems - 1;  // item of task t: last item with task0 <= t
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -87,68 +102,80 @@ __global__ void __launch_bounds__(kThreads, kBatchMinBlocks) spmm_batch_kernel(B
     p.M = it.M;
     p.nW = it.nW;
     const int w = t - bp.task0[lo];
-    bool ok;
-    if (it.vw == 1) {
-      if (it.unit)
-        ok = it.it16 ? process_range<Cfg<VT, 1, 16, true>>(p, w, wsmem, gi)
-                     : process_range<Cfg<VT, 1, 8, true>>(p, w, wsmem, gi);
-      else
-        ok = process_range<Cfg<VT, 1, 8, false>>(p, w, wsmem, gi);
-    } else if (it.vw == 2) {
-      ok = process_range<Cfg<VT, 2, 8, false>>(p, w, wsmem, gi);
+    bool ok = false;
+    if constexpr (CLASS == 0) {
+      ok = process_range<Cfg<VT, 1, 8, true>>(p, w, wsmem, gi);
+    } else if constexpr (CLASS == 1) {
+      ok = process_range<Cfg<VT, 1, 16, true>>(p, w, wsmem, gi);
     } else {
-      if constexpr (sizeof(typename Acc<VT>::T) == 4)
-        ok = process_range<Cfg<VT, 4, 8, false>>(p, w, wsmem, gi);
-      else
-        ok = false;
+      if (it.vw == 1) {
+        ok = process_range<Cfg<VT, 1, 8, false>>(p, w, wsmem, gi);
+      } else if (it.vw == 2) {
+        ok = process_range<Cfg<VT, 2, 8, false>>(p, w, wsmem, gi);
+      } else {
+        if constexpr (sizeof(typename Acc<VT>::T) == 4) ok = process_range<Cfg<VT, 4, 8, false>>(p, w, wsmem, gi);
+      }
     }
     if (!ok) return;
+    int nt = 0;
+    if ((threadIdx.x & 31) == 0) nt = nwarps + atomicAdd(bp.next, 1);
+    t = __shfl_sync(0xffffffffu, nt, 0);
   }
 }
 
-template <typename VT>
+// class of an item (see above)
+int item_class(int vw, int unit, int it16) { return unit ? (it16 ? 1 : 0) : 2; }
+
+template <typename VT, int CLASS>
 maxe_status batch_prepare(int* blocks_per_sm) {
   static int occ = -1;
   if (occ < 0) {
-    const size_t smem = batch_warp_smem<VT>() * kWarps;
-    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_batch_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = BatchClass<VT, CLASS>::warp_smem() * kWarps;
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_batch_kernel<VT, CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem)));
     int o = 0;
-    MAXE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_batch_kernel<VT>, kThreads, smem));
+    MAXE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_batch_kernel<VT, CLASS>, kThreads, smem));
     occ = o > 0 ? o : 1;
   }
   *blocks_per_sm = occ;
   return MAXE_OK;
 }
 
-template <typename VT>
+template <typename VT, int CLASS>
 maxe_status batch_launch(const BatchParams& bp, int sms, cudaStream_t st) {
   int occ = 1;
-  MAXE_TRY(batch_prepare<VT>(&occ));
+  MAXE_TRY((batch_prepare<VT, CLASS>(&occ)));
   const int64_t want = ceil_div(bp.ntasks, kWarps);
   const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * occ)));
-  spmm_batch_kernel<VT><<<grid, kThreads, batch_warp_smem<VT>() * kWarps, st>>>(bp);
+  spmm_batch_kernel<VT, CLASS><<<grid, kThreads, BatchClass<VT, CLASS>::warp_smem() * kWarps, st>>>(bp);
   MAXE_CUDA_TRY(cudaGetLastError());
   return MAXE_OK;
 }
 
-maxe_status launch_for(maxe_dtype d, const BatchParams& bp, int sms, cudaStream_t st) {
+template <typename VT>
+maxe_status batch_launch_class(int cls, const BatchParams& bp, int sms, cudaStream_t st) {
+  if (cls == 0) return batch_launch<VT, 0>(bp, sms, st);
+  if (cls == 1) return batch_launch<VT, 1>(bp, sms, st);
+  return batch_launch<VT, 2>(bp, sms, st);
+}
+
+maxe_status launch_for(maxe_dtype d, int cls, const BatchParams& bp, int sms, cudaStream_t st) {
   switch (d) {
-    case MAXE_F64: return batch_launch<double>(bp, sms, st);
-    case MAXE_F32: return batch_launch<float>(bp, sms, st);
-    case MAXE_BF16: return batch_launch<uint16_t>(bp, sms, st);
+    case MAXE_F64: return batch_launch_class<double>(cls, bp, sms, st);
+    case MAXE_F32: return batch_launch_class<float>(cls, bp, sms, st);
+    case MAXE_BF16: return batch_launch_class<uint16_t>(cls, bp, sms, st);
   }
   return MAXE_ERR_INVALID;
 }
 
-// resident warps of the batched kernel for one value type
+// resident warps of the batched kernel (class 0) for one value type
 int batch_resident_warps(maxe_dtype d, int sms) {
   int occ = 1;
   maxe_status s = MAXE_OK;
   switch (d) {
-    case MAXE_F64: s = batch_prepare<double>(&occ); break;
-    case MAXE_F32: s = batch_prepare<float>(&occ); break;
-    case MAXE_BF16: s = batch_prepare<uint16_t>(&occ); break;
+    case MAXE_F64: s = batch_prepare<double, 0>(&occ); break;
+    case MAXE_F32: s = batch_prepare<float, 0>(&occ); break;
+    case MAXE_BF16: s = batch_prepare<uint16_t, 0>(&occ); break;
   }
   if (s != MAXE_OK) occ = 1;
   return sms * occ * kWarps;
@@ -208,6 +235,7 @@ struct maxe_batch {
   int32_t* h_task0 = nullptr;
   BatchItem* d_items = nullptr;
   int32_t* d_task0 = nullptr;
+  int32_t* d_next = nullptr;  // one dynamic task counter per (value type, class) group
   cudaEvent_t uploaded = nullptr;  // the last upload from the staging has executed
   bool pending = false;
   std::vector<maxe_batch_item> items;
@@ -221,6 +249,7 @@ void batch_release(maxe_batch* b) {
     cudaEventSynchronize(b->uploaded);
     cudaEventDestroy(b->uploaded);
   }
+  b->al.put(b->d_next);
   b->al.put(b->d_task0);
   b->al.put(b->d_items);
   if (b->h_task0) cudaFreeHost(b->h_task0);
@@ -244,8 +273,8 @@ maxe_status maxe_batch_create(int32_t capacity, const maxe_allocator* alloc, voi
   b->al = Allocator(alloc, st);
   b->sms = di.sms;
   b->status = di.status;
-  // one table slot per item plus a sentinel, for each of the 3 value types
-  const size_t ni = static_cast<size_t>(capacity) * 3, nt = static_cast<size_t>(capacity + 1) * 3;
+  // one table slot per item plus a sentinel, for each (value type, kernel class)
+  const size_t ni = static_cast<size_t>(capacity) * 3 * kClasses, nt = static_cast<size_t>(capacity + 1) * 3 * kClasses;
   if (cudaMallocHost(reinterpret_cast<void**>(&b->h_items), ni * sizeof(BatchItem)) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&b->h_task0), nt * sizeof(int32_t)) != cudaSuccess) {
     cudaGetLastError();
@@ -254,7 +283,8 @@ maxe_status maxe_batch_create(int32_t capacity, const maxe_allocator* alloc, voi
   }
   b->d_items = static_cast<BatchItem*>(b->al.get(ni * sizeof(BatchItem)));
   b->d_task0 = static_cast<int32_t*>(b->al.get(nt * sizeof(int32_t)));
-  if (!b->d_items || !b->d_task0) {
+  b->d_next = static_cast<int32_t*>(b->al.get(3 * kClasses * sizeof(int32_t)));
+  if (!b->d_items || !b->d_task0 || !b->d_next) {
     batch_release(b);
     return MAXE_ERR_OOM;
   }
@@ -294,15 +324,20 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
     b->pending = false;
   }
   const maxe_dtype types[3] = {MAXE_F64, MAXE_F32, MAXE_BF16};
-  for (int ti = 0; ti < 3; ++ti) {
-    BatchItem* hi = b->h_items + static_cast<size_t>(ti) * b->capacity;
-    int32_t* ht = b->h_task0 + static_cast<size_t>(ti) * (b->capacity + 1);
+  for (int g = 0; g < 3 * kClasses; ++g) {
+    const int ti = g / kClasses, cls = g % kClasses;
+    BatchItem* hi = b->h_items + static_cast<size_t>(g) * b->capacity;
+    int32_t* ht = b->h_task0 + static_cast<size_t>(g) * (b->capacity + 1);
     int32_t m = 0;
     int64_t tasks = 0;
     for (const maxe_batch_item& a : b->items) {
       const maxe_handle* h = a.h;
       if (h->dtype != types[ti] || h->rows == 0) continue;
       const int eb = vector_bytes(h->dtype);
+      const int vw = pick_vw(a, eb);
+      const int unit = (a.k == 1 && a.ldx == 1 && a.ldy == 1) ? 1 : 0;
+      const int it16 = (unit && h->bit16) ? 1 : 0;
+      if (item_class(vw, unit, it16) != cls) continue;
       BatchItem& d = hi[m];
       d.rowptr = h->rowptr;
       d.col = h->col;
@@ -316,9 +351,9 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
       d.k = a.k;
       d.M = h->rows;
       d.nW = h->bnW;
-      d.vw = pick_vw(a, eb);
-      d.unit = (a.k == 1 && a.ldx == 1 && a.ldy == 1) ? 1 : 0;
-      d.it16 = (d.unit && h->bit16) ? 1 : 0;
+      d.vw = vw;
+      d.unit = unit;
+      d.it16 = it16;
       ht[m] = static_cast<int32_t>(tasks);
       tasks += h->bnW;
       ++m;
@@ -326,12 +361,13 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
     if (m == 0) continue;
     if (tasks > INT32_MAX) return MAXE_ERR_UNSUPPORTED;
     ht[m] = static_cast<int32_t>(tasks);
-    BatchItem* di = b->d_items + static_cast<size_t>(ti) * b->capacity;
-    int32_t* dt = b->d_task0 + static_cast<size_t>(ti) * (b->capacity + 1);
+    BatchItem* di = b->d_items + static_cast<size_t>(g) * b->capacity;
+    int32_t* dt = b->d_task0 + static_cast<size_t>(g) * (b->capacity + 1);
     MAXE_CUDA_TRY(cudaMemcpyAsync(di, hi, sizeof(BatchItem) * m, cudaMemcpyHostToDevice, st));
     MAXE_CUDA_TRY(cudaMemcpyAsync(dt, ht, sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, st));
-    BatchParams bp{di, dt, b->status, m, static_cast<int32_t>(tasks)};
-    MAXE_TRY(launch_for(types[ti], bp, b->sms, st));
+    MAXE_CUDA_TRY(cudaMemsetAsync(b->d_next + g, 0, sizeof(int32_t), st));
+    BatchParams bp{di, dt, b->status, b->d_next + g, m, static_cast<int32_t>(tasks)};
+    MAXE_TRY(launch_for(types[ti], cls, bp, b->sms, st));
   }
   if (cap == cudaStreamCaptureStatusNone) {
     MAXE_CUDA_TRY(cudaEventRecord(b->uploaded, st));
@@ -355,32 +391,42 @@ maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
   void* Y = scratch.get<unsigned char>(static_cast<size_t>(h->rows) * k * eb);
   if (!X || !Y) return MAXE_ERR_OOM;
   MAXE_CUDA_TRY(cudaMemsetAsync(X, 0, static_cast<size_t>(h->cols) * k * eb, st));
+  constexpr int kMaxCopies = 64;
   maxe_batch* b = nullptr;
-  MAXE_TRY(maxe_batch_create(1, nullptr, stream, &b));
+  MAXE_TRY(maxe_batch_create(kMaxCopies, nullptr, stream, &b));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   maxe_status s = (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) ? MAXE_OK
                                                                                              : MAXE_ERR_CUDA;
-  const int64_t floor_h = ceil_div(h->nnz, batch_resident_warps(h->dtype, h->sms));
-  const int64_t cand_h[3] = {std::max<int64_t>(512, floor_h), std::max<int64_t>(2048, floor_h),
-                             std::max<int64_t>(8192, floor_h)};
+  const int64_t resident = batch_resident_warps(h->dtype, h->sms);
+  const int64_t floor_h = ceil_div(h->nnz, resident);
+  const int64_t cand_h[4] = {std::max<int64_t>(512, floor_h), std::max<int64_t>(2048, floor_h),
+                             std::max<int64_t>(8192, floor_h), std::max<int64_t>(32768, floor_h)};
   float best = 1e30f;
   int64_t best_h = cand_h[1];
   int best_it = 0;
-  maxe_batch_item item{h, k, X, k, Y, k, 0u};
-  for (int ci = 0; ci < 3 && s == MAXE_OK; ++ci) {
+  // Throughput, not latency: the matrix is timed as one of many items, so the
+  // item is repeated until its tasks fill the GPU a few times over (the copies
+  // write identical values to one Y; only the time is used).
+  maxe_batch_item items[kMaxCopies];
+  for (int ci = 0; ci < 4 && s == MAXE_OK; ++ci) {
+    if (ci > 0 && cand_h[ci] == cand_h[ci - 1]) continue;
     for (int it16 = 0; it16 <= (k == 1 ? 1 : 0) && s == MAXE_OK; ++it16) {
       s = batch_plan(h, cand_h[ci], it16, st);
-      if (s == MAXE_OK) s = maxe_batch_set(b, &item, 1);
+      if (s != MAXE_OK) break;
+      const int64_t copies = std::max<int64_t>(1, std::min<int64_t>(kMaxCopies, ceil_div(4 * resident, h->bnW)));
+      for (int64_t c = 0; c < copies; ++c) items[c] = maxe_batch_item{h, k, X, k, Y, k, 0u};
+      s = maxe_batch_set(b, items, static_cast<int32_t>(copies));
       for (int rep = 0; rep < 2 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
       if (s != MAXE_OK) break;
       cudaEventRecord(e0, st);
-      for (int rep = 0; rep < 5 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
+      for (int rep = 0; rep < 3 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) s = MAXE_ERR_CUDA;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (s == MAXE_OK && ms < best) {
-        best = ms;
+      const float per_copy = ms / static_cast<float>(copies);
+      if (s == MAXE_OK && per_copy < best) {
+        best = per_copy;
         best_h = cand_h[ci];
         best_it = it16;
       }

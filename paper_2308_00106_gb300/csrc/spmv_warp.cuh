@@ -46,13 +46,16 @@ struct Params {
   int32_t k, M, nW;
 };
 
+// X[c, c0 .. c0+VW) into xv.  A group past column k is read as a whole vector
+// when the row is padded (ldx >= c0 + VW: still inside the row) and the unused
+// lanes are zeroed; otherwise the tail columns are read one by one.
 template <int VW, typename AT>
 __device__ __forceinline__ void xload(const AT* __restrict__ X, int32_t c, int64_t ldx, int c0, int k, AT (&xv)[VW]) {
   const AT* px = X + static_cast<int64_t>(c) * ldx + c0;
   if constexpr (VW == 1) {
     xv[0] = __ldg(px);
   } else {
-    if (c0 + VW <= k) {
+    if (c0 + VW <= k || c0 + VW <= ldx) {
       if constexpr (VW == 2 && sizeof(AT) == 4) {
         const float2 u = __ldg(reinterpret_cast<const float2*>(px));
         xv[0] = u.x, xv[1] = u.y;
@@ -62,6 +65,11 @@ __device__ __forceinline__ void xload(const AT* __restrict__ X, int32_t c, int64
       } else {
         const float4 u = __ldg(reinterpret_cast<const float4*>(px));
         xv[0] = u.x, xv[1] = u.y, xv[2] = u.z, xv[3] = u.w;
+      }
+      if (c0 + VW > k) {
+#pragma unroll
+        for (int w = 0; w < VW; ++w)
+          if (c0 + w >= k) xv[w] = AT(0);
       }
     } else {
 #pragma unroll
@@ -116,33 +124,90 @@ constexpr size_t block_smem() {
   return sizeof(WarpSmem<VT, VW, IT>) * kWarps;
 }
 
+// A lane's N 16-byte words of a piece in shared memory, read without bank
+// conflicts: lanes of one 8-lane access phase sit N words apart, so lane l
+// starts at word (l*N/8) mod N and the loaded words are rotated back in
+// registers (log2 N select stages).
+template <int N>
+__device__ __forceinline__ void lds_words(const uint4* base, uint4 (&w)[N], int lane) {
+  const int rot = ((lane * N) >> 3) & (N - 1);
+#pragma unroll
+  for (int q = 0; q < N; ++q) w[q] = base[(q + rot) & (N - 1)];
+#pragma unroll
+  for (int bit = 1; bit < N; bit <<= 1) {
+    if (rot & bit) {
+      uint4 t[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) t[i] = w[(i - bit + N) & (N - 1)];
+#pragma unroll
+      for (int i = 0; i < N; ++i) w[i] = t[i];
+    }
+  }
+}
+
 template <int IT>
-__device__ __forceinline__ void lds_vals(const float* p, float (&a)[IT]) {
+__device__ __forceinline__ void lds_cols(const int32_t* p, int32_t (&c)[IT], int lane) {
+  uint4 w[IT / 4];
+  lds_words<IT / 4>(reinterpret_cast<const uint4*>(p), w, lane);
 #pragma unroll
   for (int i = 0; i < IT / 4; ++i) {
-    const float4 u = reinterpret_cast<const float4*>(p)[i];
-    a[4 * i] = u.x, a[4 * i + 1] = u.y, a[4 * i + 2] = u.z, a[4 * i + 3] = u.w;
+    c[4 * i] = static_cast<int32_t>(w[i].x), c[4 * i + 1] = static_cast<int32_t>(w[i].y);
+    c[4 * i + 2] = static_cast<int32_t>(w[i].z), c[4 * i + 3] = static_cast<int32_t>(w[i].w);
+  }
+}
+
+template <int IT>
+__device__ __forceinline__ void lds_vals(const float* p, float (&a)[IT], int lane) {
+  uint4 w[IT / 4];
+  lds_words<IT / 4>(reinterpret_cast<const uint4*>(p), w, lane);
+#pragma unroll
+  for (int i = 0; i < IT / 4; ++i) {
+    a[4 * i] = __uint_as_float(w[i].x), a[4 * i + 1] = __uint_as_float(w[i].y);
+    a[4 * i + 2] = __uint_as_float(w[i].z), a[4 * i + 3] = __uint_as_float(w[i].w);
   }
 }
 template <int IT>
-__device__ __forceinline__ void lds_vals(const double* p, double (&a)[IT]) {
+__device__ __forceinline__ void lds_vals(const double* p, double (&a)[IT], int lane) {
+  uint4 w[IT / 2];
+  lds_words<IT / 2>(reinterpret_cast<const uint4*>(p), w, lane);
 #pragma unroll
   for (int i = 0; i < IT / 2; ++i) {
-    const double2 u = reinterpret_cast<const double2*>(p)[i];
-    a[2 * i] = u.x, a[2 * i + 1] = u.y;
+    a[2 * i] = __hiloint2double(static_cast<int>(w[i].y), static_cast<int>(w[i].x));
+    a[2 * i + 1] = __hiloint2double(static_cast<int>(w[i].w), static_cast<int>(w[i].z));
   }
 }
 template <int IT>
-__device__ __forceinline__ void lds_vals(const uint16_t* p, float (&a)[IT]) {
+__device__ __forceinline__ void lds_vals(const uint16_t* p, float (&a)[IT], int lane) {
+  uint4 w[IT / 8];
+  lds_words<IT / 8>(reinterpret_cast<const uint4*>(p), w, lane);
 #pragma unroll
   for (int i = 0; i < IT / 8; ++i) {
-    const uint4 u = reinterpret_cast<const uint4*>(p)[i];
-    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+    const uint32_t w4[4] = {w[i].x, w[i].y, w[i].z, w[i].w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       a[8 * i + 2 * q] = __uint_as_float(w4[q] << 16);
       a[8 * i + 2 * q + 1] = __uint_as_float(w4[q] & 0xFFFF0000u);
     }
+  }
+}
+
+// Scanned sums of a piece are stored transposed, entry e = IT*lane + j at slot
+// (j*32 + lane): a warp's stores of one j are consecutive (conflict-free).
+template <int IT, int VW>
+__device__ __forceinline__ int sum_slot(int e) {
+  return ((e % IT) * 32 + e / IT) * VW;
+}
+
+template <int VW, typename AT>
+__device__ __forceinline__ void sts_vec(AT* p, const AT (&v)[VW]) {
+  if constexpr (VW == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (VW == 2 && sizeof(AT) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (VW == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+    *p = v[0];
   }
 }
 
@@ -237,12 +302,8 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
     if (!__all_sync(0xffffffffu, ok)) return false;
     int32_t cj[kItems];
     AT a[kItems];
-#pragma unroll
-    for (int q = 0; q < kItems / 4; ++q) {
-      const int4 u = reinterpret_cast<const int4*>(ws.col[s] + kItems * lane)[q];
-      cj[4 * q] = u.x, cj[4 * q + 1] = u.y, cj[4 * q + 2] = u.z, cj[4 * q + 3] = u.w;
-    }
-    lds_vals<IT>(ws.val[s] + kItems * lane, a);
+    lds_cols<IT>(ws.col[s] + kItems * lane, cj, lane);
+    lds_vals<IT>(ws.val[s] + kItems * lane, a, lane);
     __syncwarp();
     if (lane < kPiece / 32) ws.flags[lane] = 0u;  // every lane has its flag bits
     // entries outside [e_lo, e_hi) belong to other warps (first and last piece only)
@@ -316,9 +377,7 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
 #pragma unroll
           for (int u = 0; u < VW; ++u) v[j][u] += P[u];
 #pragma unroll
-      for (int j = 0; j < kItems; ++j)
-#pragma unroll
-        for (int u = 0; u < VW; ++u) ws.sums[(kItems * lane + j) * VW + u] = v[j][u];
+      for (int j = 0; j < kItems; ++j) sts_vec<VW>(ws.sums + (j * 32 + lane) * VW, v[j]);
       __syncwarp();
       // rows that end in the piece
       int32_t prev_end = r_start;
@@ -331,7 +390,7 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
         if (b + lane < nend) {
           AT out[VW];
           if (end > start) {
-            const AT* src = ws.sums + (end - base - 1) * VW;
+            const AT* src = ws.sums + sum_slot<IT, VW>(end - base - 1);
 #pragma unroll
             for (int u = 0; u < VW; ++u) out[u] = src[u];
           } else {
@@ -347,7 +406,7 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
         prev_end = __shfl_sync(0xffffffffu, end, 31);
       }
       // partial row running on into the next piece
-      if (lane < VW) ws.carry[c0 + lane] = (last_o == kPiece) ? AT(0) : ws.sums[(kPiece - 1) * VW + lane];
+      if (lane < VW) ws.carry[c0 + lane] = (last_o == kPiece) ? AT(0) : ws.sums[sum_slot<IT, VW>(kPiece - 1) + lane];
       __syncwarp();
     }
     if (nend > 0) r_start = base + last_o;

@@ -17,10 +17,11 @@ step in its kernels (maxe_vec_norm_gather / maxe_vec_dot_gather).
 
 Continuous batching: requests are admitted as soon as their buffers fit under
 the device-memory cap; each batch step takes one unit of work (a product) from
-every admitted request that is not already on the GPU, so requests join and
-leave between steps and a power iteration advances one product per step.  Two
-CUDA streams, each with its own batch object, keep two steps in flight, so a
-step's work overlaps the previous one on the device.  Every matrix has a fixed
+admitted requests that are not already on the GPU, oldest first, up to a byte
+budget of work per step, so requests join and leave between steps and a power
+iteration advances one product per step.  Two CUDA streams, each with its own
+batch object, keep two steps in flight, so a step's work overlaps the previous
+one on the device.  Every matrix has a fixed
 batch plan, so a request's result is bit-identical alone and in any mix.
 """
 from __future__ import annotations
@@ -86,7 +87,7 @@ class Server:
     """Resident permuted matrices + the continuous-batching loop."""
 
     def __init__(self, mats, seed: int = 2308, mem_cap_bytes: int = 60 << 30, streams: int = 2,
-                 tune: bool = True, batch_capacity: int = 4096):
+                 tune: bool = False, batch_capacity: int = 4096, step_bytes: int = 2 << 30):
         maxe.load(build_if_missing=True)
         self.mats = mats
         self.handles, self.Q, self.perm_c = [], [], []
@@ -112,11 +113,12 @@ class Server:
         self.adm_stream = torch.cuda.Stream()  # initialises admitted requests' buffers
         self.batches = [maxe.Batch(batch_capacity, stream=s) for s in self.streams]
         self.capacity = batch_capacity
+        self.step_bytes = step_bytes  # work per batch step, so that the streams alternate and overlap
 
     # ---------------------------------------------------------------- helpers
     def request_bytes(self, r: Request) -> int:
         A = self.mats[r.mat]
-        b = (A.cols + A.rows) * r.k * 4
+        b = (A.cols + A.rows) * ((r.k + 3) // 4 * 4) * 4
         if r.kind == "power":
             b += (A.cols + A.rows) * 4 + 1024 * 8
         return b
@@ -137,8 +139,10 @@ class Server:
                           "scratch": torch.empty(1024, dtype=torch.float64, device="cuda"),
                           "lam": torch.empty(1, dtype=torch.float64, device="cuda"), "u0": u.clone()}
             else:
-                X = torch.rand(A.cols, r.k, generator=g, device="cuda") * 2 - 1
-                r.bufs = {"X": X, "Y": torch.empty(A.rows, r.k, device="cuda")}
+                kp = (r.k + 3) // 4 * 4  # 16-byte rows: the kernel gathers 4 columns per load
+                X = torch.zeros(A.cols, kp, device="cuda")
+                X[:, :r.k] = torch.rand(A.cols, r.k, generator=g, device="cuda") * 2 - 1
+                r.bufs = {"X": X[:, :r.k], "Y": torch.empty(A.rows, kp, device="cuda")[:, :r.k]}
 
     def _launch(self, si: int, reqs):
         s = self.streams[si]
@@ -170,12 +174,14 @@ class Server:
             if r.kind == "power":
                 r.result = (float(r.bufs["lam"].item()), r.bufs["u"].clone(), r.bufs["u0"])
             else:
-                r.result = r.bufs["Y"].clone()
+                r.result = r.bufs["Y"].contiguous()
         r.bufs = {}
 
     # ------------------------------------------------------------ the loop
-    def run(self, trace, keep_results: bool = False, max_wall: float = 600.0):
-        """Serve `trace` (requests sorted by arrival); returns a stats dict."""
+    def run(self, trace, keep_results: bool = False, max_wall: float = 600.0, max_items: int | None = None):
+        """Serve `trace` (requests sorted by arrival); returns a stats dict.
+        max_items caps the requests per batch step (1 = no batching)."""
+        cap_items = self.capacity if max_items is None else max(1, min(max_items, self.capacity))
         trace = sorted(trace, key=lambda r: r.arrival)
         n = len(trace)
         for r in trace:
@@ -227,7 +233,11 @@ class Server:
             for si in range(len(self.streams)):
                 if si in inflight or not ready:
                     continue
-                take = [ready.popleft() for _ in range(min(len(ready), self.capacity))]
+                take, work = [], 0
+                while ready and len(take) < cap_items and (not take or work < self.step_bytes):
+                    r = ready.popleft()
+                    take.append(r)
+                    work += self.unit_bytes(r)
                 # the first step of a freshly admitted request must see its initialised buffers
                 self.streams[si].wait_stream(self.adm_stream)
                 inflight[si] = (self._launch(si, take), take)

@@ -178,6 +178,15 @@ def test_spmm_against_oracle(k, dtype):
     Ypo = oracle.spmm(A.rows, nrp, nco, nva, code(dtype), Xp.cpu().numpy())
     assert rel_l2(Ybig[:, :k].cpu().numpy(), Ypo) <= TOL[dtype]
     assert torch.all(Ybig[:, k:] == 7.0)
+    # leading dimensions padded to whole vectors: the tail column group is read
+    # as a full vector (padding ignored) and written column by column
+    kp = (k + 3) // 4 * 4
+    Xpad = torch.full((A.cols, kp), float("nan"), dtype=X.dtype, device="cuda")
+    Xpad[:, :k] = Xp
+    Ypad = torch.full((A.rows, kp), 5.0, dtype=X.dtype, device="cuda")
+    maxe.maxe_spmm(h, Xpad[:, :k], Ypad[:, :k], permuted=True)
+    assert rel_l2(Ypad[:, :k].cpu().numpy(), Ypo) <= TOL[dtype]
+    assert torch.all(Ypad[:, k:] == 5.0)
 
 
 def test_spmm_columns_match_spmv():
