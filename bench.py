@@ -62,7 +62,7 @@ def traffic_from_profile(name):
     return t, kernel_rev
 
 
-KERNEL_REVISION = "spmm_warp_kernel r2"  # bump whenever the SpMV kernel changes
+KERNEL_REVISION = "spmm_warp_kernel r3"  # bump whenever the SpMV kernel changes
 
 
 class Clocks:
@@ -440,17 +440,90 @@ def run_serving(args):
         print(json.dumps(out))
 
 
+def run_laplacian_table(args):
+    """5-point Laplacian, n = 4096 (16.8M rows, 83.9M nonzeros): FP64 / FP32 /
+    BF16 values x natural / permuted order x SpMM k = 1, 4, 16."""
+    import oracle
+    from paper_2308_00106_gb300 import maxe
+    from paper_2308_00106_gb300 import workloads as W
+
+    rank, world, local = dist_setup(args)
+    maxe.load(build_if_missing=(rank == 0))
+    n = 4096
+    hbm, src = peaks()
+    rows_out = []
+    base = W.laplacian5(n, "f64", "cuda")
+    M = N = base.rows
+    rperm = maxe.maxe_build_permutation(args.seed, M, 0)
+    cperm = maxe.maxe_build_permutation(args.seed, N, 1)
+    sample = np.random.default_rng(0).choice(M, size=2000, replace=False)
+    K = max(10, args.steps // 200)
+    clocks = Clocks(local)
+    clocks.start()
+    for dtype in ("f64", "f32", "bf16"):
+        A = base.astype(dtype)
+        vb = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
+        xb = 8 if dtype == "f64" else 4
+        vdt = torch.float64 if dtype == "f64" else torch.float32
+        for order in ("natural", "permuted"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = maxe.from_csr(A, rperm, cperm, autotune=True) if order == "permuted" else maxe.from_csr(A, autotune=True)
+            torch.cuda.synchronize()
+            t_build = time.perf_counter() - t0
+            nrp, ncol, nval, _, _ = h.csr()
+            vv = nval.cpu()
+            vv = vv.view(torch.int16).numpy().view(np.uint16) if dtype == "bf16" else vv.numpy()
+            rp_h, col_h = nrp.cpu().numpy(), ncol.cpu().numpy()
+            for k in (1, 4, 16):
+                kp = (k + 3) // 4 * 4 if k > 1 else 1
+                Xb = torch.zeros(N, kp, dtype=vdt, device="cuda")
+                Xb[:, :k] = W.matrix_rhs(k, N, k, "f64" if dtype == "f64" else "f32", "cuda")
+                X = Xb[:, :k]
+                Y = torch.empty(M, kp, dtype=vdt, device="cuda")[:, :k]
+                if k == 1:
+                    x1 = Xb[:, 0].contiguous()
+                    y1 = torch.empty(M, dtype=vdt, device="cuda")
+                    step = lambda: maxe.maxe_spmv(h, x1, y1, permuted=True)  # noqa: E731
+                else:
+                    step = lambda: maxe.maxe_spmm(h, X, Y, permuted=True)  # noqa: E731
+                ms = timed_steps(step, K, 3, world, graph_len=5)
+                by = alg_bytes(M, N, A.nnz, vb, xb, xb, k)
+                gbs = by / (ms * 1e-3) / 1e9
+                out_cols = (y1.view(-1, 1) if k == 1 else Y)
+                errs = []
+                for c in sorted({0, k - 1}):
+                    ref = oracle.spmv_rows(rp_h, col_h, vv, W.DTYPE_CODE[dtype],
+                                           Xb[:, c].cpu().double().numpy(), sample)
+                    got = out_cols[:, c].cpu().double().numpy()[sample]
+                    errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+                rows_out.append({"dtype": dtype, "order": order, "k": k, "ms": round(ms, 4), "gbs": round(gbs, 1),
+                                 "frac": round(gbs / hbm, 4), "gflops": round(2 * A.nnz * k / (ms * 1e-3) / 1e9, 1),
+                                 "rel_l2_sampled": max(errs), "items_per_lane": h.items_per_lane(),
+                                 "build_s": round(t_build, 4)})
+            h.close()
+    clk = clocks.stop()
+    out = {"metric": "SpMV/SpMM GB/s and frac of HBM roofline, 5-point Laplacian n=4096 (config 3)",
+           "unit": "GB/s", "peak": hbm, "peak_source": src, "rows": M, "nnz": base.nnz,
+           "timing": f"{K} steps, CUDA graph of 5, CUDA events; inputs larger than L2 (matrix >= 0.5 GB)",
+           "table": rows_out, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["maxe", "reference"], default="maxe")
-    ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag", "batched", "serving"],
-                    default="powerlaw")
+    ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag", "batched", "serving",
+                                           "laplacian-table"], default="powerlaw")
     ap.add_argument("--requests", type=int, default=1500, help="requests per serving trace")
     ap.add_argument("--batch-count", type=int, default=256, help="matrices of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: default batch plans, no autotuning")
+    ap.add_argument("--items-per-lane", choices=["auto", "8", "16"], default="auto",
+                    help="SpMV kernel variant: autotuned per handle, or fixed")
     ap.add_argument("--seed", type=int, default=2308)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -465,6 +538,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "laplacian-table":
+        return run_laplacian_table(args)
 
     import oracle
     from paper_2308_00106_gb300 import maxe
@@ -485,9 +560,11 @@ def main():
     rperm = maxe.maxe_build_permutation(args.seed, M, 0)
     cperm = maxe.maxe_build_permutation(args.seed, N, 1)
     ev[1].record()
-    hP = maxe.from_csr(A, rperm, cperm, autotune=not args.profile)
+    tune = args.items_per_lane == "auto"
+    i16 = args.items_per_lane == "16"
+    hP = maxe.from_csr(A, rperm, cperm, autotune=tune, items16=i16)
     ev[2].record()
-    hN = maxe.from_csr(A, autotune=not args.profile)
+    hN = maxe.from_csr(A, autotune=tune, items16=i16)
     ev[3].record()
     torch.cuda.synchronize()
     t_perm, t_pcsr = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
