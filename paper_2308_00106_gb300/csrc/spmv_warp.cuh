@@ -324,9 +324,12 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
 
     for (int g = 0; g < ngroups; ++g) {
       const int c0 = g * VW;
+      // products fused with the serial segmented scan over the lane's entries:
+      // v[j] = a_j x_j + (j starts a row ? 0 : v[j-1])  -- one FMA per entry
       AT v[kItems][VW];
 #pragma unroll
       for (int j = 0; j < kItems; ++j) {
+        const bool head = j == 0 || ((fw >> j) & 1u);
         if ((vmask >> j) & 1u) {
           AT xv[VW];
           if constexpr (UNIT) {
@@ -335,17 +338,12 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
             xload<VW>(X, cj[j], p.ldx, c0, k, xv);
           }
 #pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] = a[j] * xv[u];
+          for (int u = 0; u < VW; ++u) v[j][u] = head ? a[j] * xv[u] : fma(a[j], xv[u], v[j > 0 ? j - 1 : 0][u]);
         } else {
 #pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] = AT(0);
+          for (int u = 0; u < VW; ++u) v[j][u] = head ? AT(0) : v[j > 0 ? j - 1 : 0][u];
         }
       }
-#pragma unroll
-      for (int j = 1; j < kItems; ++j)
-        if (!((fw >> j) & 1u))
-#pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] += v[j - 1][u];
       int F = fw != 0u;
       AT V[VW];
 #pragma unroll
@@ -372,12 +370,15 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
         P[u] = (lane == 0) ? cin : (Fe ? Ve : cin + Ve);
       }
 #pragma unroll
-      for (int j = 0; j < kItems; ++j)
-        if (j < first_flag)
-#pragma unroll
-          for (int u = 0; u < VW; ++u) v[j][u] += P[u];
-#pragma unroll
       for (int j = 0; j < kItems; ++j) sts_vec<VW>(ws.sums + (j * 32 + lane) * VW, v[j]);
+      // The prefix P belongs to the lane's leading segment [0, first_flag); the
+      // only entry of it that is ever read (a row end, or the piece's carry) is
+      // its last one, so P is added there alone.
+      if (first_flag > 0) {
+        AT* q = ws.sums + ((first_flag - 1) * 32 + lane) * VW;
+#pragma unroll
+        for (int u = 0; u < VW; ++u) q[u] += P[u];
+      }
       __syncwarp();
       // rows that end in the piece
       int32_t prev_end = r_start;
