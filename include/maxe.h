@@ -63,12 +63,19 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * are in range and perms are bijections (synchronises; MAXE_ERR_INVALID on failure). */
 #define MAXE_VALIDATE 0x2u
 /* Flag of maxe_permute_csr: time the SpMV kernel variants (8 or 16 entries
- * per lane) on this matrix and keep the faster one for the handle
+ * per lane) on this matrix and keep the faster one for the handle; also time
+ * the two SpMM paths (column passes, or columns across lanes) at k = 16 when
+ * their scratch (rows + cols) * 16 vectors fits in 3 GiB, and keep the faster
  * (synchronises; a few products of device time). */
 #define MAXE_AUTOTUNE 0x4u
 /* Flag of maxe_permute_csr: use the 16-entries-per-lane SpMV variant without
  * timing (tuning override; MAXE_AUTOTUNE takes precedence). */
 #define MAXE_ITEMS16 0x8u
+/* Flag of maxe_permute_csr: SpMM with columns across lanes (groups of lanes
+ * hold the k columns, each walks consecutive entries) instead of column passes,
+ * for k >= 5 (FP32 vectors) / k >= 3 (FP64) with 16-byte rows of X and Y
+ * (tuning override; MAXE_AUTOTUNE takes precedence). */
+#define MAXE_SPMM_LANES 0x10u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -124,7 +131,7 @@ MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_
  * cinv[c]; each row is then sorted by new column (stable).  Values are copied
  * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
  * (the "plain" matrix).  The handle keeps its own copies of the permutations.
- * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16.  *out receives the new handle.
+ * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16, MAXE_SPMM_LANES.  *out receives the new handle.
  * Synchronises `stream` once (to size the pass over rows longer than 2048).
  * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
 MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
@@ -137,8 +144,9 @@ MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, c
 MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, const int32_t** rperm,
                             const int32_t** cperm);
 
-/* Entries per lane of the handle's SpMV kernel variant (8 or 16), as chosen
- * by MAXE_AUTOTUNE / MAXE_ITEMS16 at creation.  items: (host). */
+/* Kernel variants of the handle, as chosen by MAXE_AUTOTUNE / MAXE_ITEMS16 /
+ * MAXE_SPMM_LANES at creation: *items = entries per lane of the SpMV variant
+ * (8 or 16), plus 0x100 when SpMM uses columns across lanes.  items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;

@@ -127,7 +127,8 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (bad_size(A->rows) || bad_size(A->cols) || bad_size(A->nnz) || bad_dtype(A->dtype)) return MAXE_ERR_INVALID;
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return MAXE_ERR_INVALID;
   if (A->nnz > 0 && (A->rows == 0 || A->cols == 0)) return MAXE_ERR_INVALID;
-  if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16)) return MAXE_ERR_INVALID;
+  if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16 | MAXE_SPMM_LANES))
+    return MAXE_ERR_INVALID;
   DeviceInfo di{};
   MAXE_TRY(device_info(&di));
   cudaStream_t st = as_stream(stream);
@@ -145,7 +146,9 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
   if (s == MAXE_OK) s = batch_plan_default(h, st);
   if (s == MAXE_OK && (flags & MAXE_ITEMS16)) h->spmv_items16 = 1;
+  if (s == MAXE_OK && (flags & MAXE_SPMM_LANES)) h->spmm_lc = 1;
   if (s == MAXE_OK && (flags & MAXE_AUTOTUNE)) s = spmv_autotune(h, st);
+  if (s == MAXE_OK) h->blc = h->spmm_lc;  // the default batch plan follows the handle's SpMM path
   if (s != MAXE_OK) {
     release(h);
     return s;
@@ -170,7 +173,7 @@ maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view, const int32_t*
 
 maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
   if (!h || !items) return MAXE_ERR_INVALID;
-  *items = h->spmv_items16 ? 16 : 8;
+  *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0);
   return MAXE_OK;
 }
 

@@ -38,7 +38,7 @@ struct BatchItem {
   const int32_t* yperm;
   const int32_t* wrow;
   int64_t ldx, ldy;
-  int32_t k, M, nW, vw, it16, unit;
+  int32_t k, M, nW, vw, it16, unit, lcg;
 };
 
 struct BatchParams {
@@ -65,6 +65,7 @@ struct BatchClass {
     if (CLASS == 1) m = sizeof(WarpSmem<VT, 1, 16>);
     if (CLASS == 2) {
       m = std::max(sizeof(WarpSmem<VT, 1, 8>), sizeof(WarpSmem<VT, 2, 8>));
+      m = std::max(m, sizeof(WarpSmemLC<VT>));
       if (sizeof(typename Acc<VT>::T) == 4) m = std::max(m, sizeof(WarpSmem<VT, 4, 8>));
     }
     return (m + 127) & ~size_t(127);
@@ -108,7 +109,9 @@ __global__ void __launch_bounds__(kThreads, BatchClass<VT, CLASS>::kMinBlocks) s
     } else if constexpr (CLASS == 1) {
       ok = process_range<Cfg<VT, 1, 16, true>>(p, w, wsmem, gi);
     } else {
-      if (it.vw == 1) {
+      if (it.lcg > 0) {
+        ok = process_range_lc<VT>(p, w, wsmem, gi, it.lcg);
+      } else if (it.vw == 1) {
         ok = process_range<Cfg<VT, 1, 8, false>>(p, w, wsmem, gi);
       } else if (it.vw == 2) {
         ok = process_range<Cfg<VT, 2, 8, false>>(p, w, wsmem, gi);
@@ -196,7 +199,7 @@ int pick_vw(const maxe_batch_item& a, int eb) {
 }  // namespace
 
 // Batch plan of a handle: a partition with H_b entries per warp task.
-maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st) {
+maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc) {
   H = std::max<int64_t>(256, H);
   const int64_t nW = std::max<int64_t>(1, ceil_div(h->nnz, H));
   int32_t* w = static_cast<int32_t*>(h->al.get(static_cast<size_t>(nW + 1) * sizeof(int32_t)));
@@ -212,12 +215,14 @@ maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st) {
   h->bnW = static_cast<int32_t>(nW);
   h->bH = H;
   h->bit16 = it16;
+  h->blc = lc;
   return MAXE_OK;
 }
 
 maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st) {
   const int64_t target = batch_resident_warps(h->dtype, h->sms);
-  return batch_plan(h, std::max<int64_t>(kDefaultBatchTask, ceil_div(std::max<int64_t>(h->nnz, 1), target)), 0, st);
+  return batch_plan(h, std::max<int64_t>(kDefaultBatchTask, ceil_div(std::max<int64_t>(h->nnz, 1), target)), 0, st,
+                    0);
 }
 
 }  // namespace maxe
@@ -354,6 +359,8 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
       d.vw = vw;
       d.unit = unit;
       d.it16 = it16;
+      d.lcg = (unit || !h->blc) ? 0 : lc_group(a.k, eb, static_cast<int>(a.ldx % 1024), static_cast<int>(a.ldy % 1024));
+      if (d.lcg > 0 && vw < (eb == 4 ? 4 : 2)) d.lcg = 0;  // needs 16-byte aligned X and Y rows
       ht[m] = static_cast<int32_t>(tasks);
       tasks += h->bnW;
       ++m;
@@ -386,11 +393,13 @@ maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
   if (h->rows == 0 || h->nnz == 0) return MAXE_OK;
   cudaStream_t st = as_stream(stream);
   const int eb = vector_bytes(h->dtype);
+  // rows padded to whole vectors, as callers are advised to lay X and Y out
+  const int32_t kp = k == 1 ? 1 : static_cast<int32_t>(round_up(k, eb == 4 ? 4 : 2));
   ScratchSet scratch(h->al);
-  void* X = scratch.get<unsigned char>(static_cast<size_t>(h->cols) * k * eb);
-  void* Y = scratch.get<unsigned char>(static_cast<size_t>(h->rows) * k * eb);
+  void* X = scratch.get<unsigned char>(static_cast<size_t>(h->cols) * kp * eb);
+  void* Y = scratch.get<unsigned char>(static_cast<size_t>(h->rows) * kp * eb);
   if (!X || !Y) return MAXE_ERR_OOM;
-  MAXE_CUDA_TRY(cudaMemsetAsync(X, 0, static_cast<size_t>(h->cols) * k * eb, st));
+  MAXE_CUDA_TRY(cudaMemsetAsync(X, 0, static_cast<size_t>(h->cols) * kp * eb, st));
   constexpr int kMaxCopies = 64;
   maxe_batch* b = nullptr;
   MAXE_TRY(maxe_batch_create(kMaxCopies, nullptr, stream, &b));
@@ -403,18 +412,21 @@ maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
                              std::max<int64_t>(8192, floor_h), std::max<int64_t>(32768, floor_h)};
   float best = 1e30f;
   int64_t best_h = cand_h[1];
-  int best_it = 0;
+  int best_it = 0, best_lc = 0;
   // Throughput, not latency: the matrix is timed as one of many items, so the
   // item is repeated until its tasks fill the GPU a few times over (the copies
   // write identical values to one Y; only the time is used).
   maxe_batch_item items[kMaxCopies];
   for (int ci = 0; ci < 4 && s == MAXE_OK; ++ci) {
     if (ci > 0 && cand_h[ci] == cand_h[ci - 1]) continue;
-    for (int it16 = 0; it16 <= (k == 1 ? 1 : 0) && s == MAXE_OK; ++it16) {
-      s = batch_plan(h, cand_h[ci], it16, st);
+    for (int var = 0; var <= 1 && s == MAXE_OK; ++var) {
+      // second variant: 16 entries per lane for k = 1, columns across lanes for k > 1
+      const int it16 = (k == 1) ? var : 0, lc = (k > 1) ? var : 0;
+      if (var == 1 && k > 1 && lc_group(k, eb, kp % 1024, kp % 1024) == 0) continue;
+      s = batch_plan(h, cand_h[ci], it16, st, lc);
       if (s != MAXE_OK) break;
       const int64_t copies = std::max<int64_t>(1, std::min<int64_t>(kMaxCopies, ceil_div(4 * resident, h->bnW)));
-      for (int64_t c = 0; c < copies; ++c) items[c] = maxe_batch_item{h, k, X, k, Y, k, 0u};
+      for (int64_t c = 0; c < copies; ++c) items[c] = maxe_batch_item{h, k, X, kp, Y, kp, 0u};
       s = maxe_batch_set(b, items, static_cast<int32_t>(copies));
       for (int rep = 0; rep < 2 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
       if (s != MAXE_OK) break;
@@ -429,13 +441,14 @@ maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
         best = per_copy;
         best_h = cand_h[ci];
         best_it = it16;
+        best_lc = lc;
       }
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   maxe_batch_destroy(b);
-  if (s == MAXE_OK) s = batch_plan(h, best_h, best_it, st);
+  if (s == MAXE_OK) s = batch_plan(h, best_h, best_it, st, best_lc);
   if (s == MAXE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = MAXE_ERR_CUDA;
   return s;
 }

@@ -26,10 +26,12 @@ struct maxe_handle {
   int32_t* wrow[2] = {nullptr, nullptr};  // per SpMV variant (8 / 16 entries per lane)
   int32_t nW[2] = {0, 0};
   int spmv_items16 = 0;                    // chosen SpMV variant (autotuned or 0)
+  int spmm_lc = 0;                         // SpMM with columns across lanes (autotuned or 0)
   int32_t* bwrow = nullptr;                // batch plan: partition with bH entries per warp task
   int32_t bnW = 0;
   int64_t bH = 0;
   int bit16 = 0;                           // batch plan: 16 entries per lane for k = 1
+  int blc = 0;                             // batch plan: SpMM with columns across lanes
   void* xbuf = nullptr;  // cols * k_cap vector elements
   int32_t xbuf_k = 0;
   maxe::Allocator al;
@@ -48,15 +50,16 @@ int64_t spmv_pad_elems();
 maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st);
 // Y = A' X (rows of Y optionally scattered through yperm).  X: cols x k (ldx),
 // Y: rows x k (ldy), vector element type of the handle.
-// variant: -1 = the handle's choice, 0 / 1 = force 8 / 16 entries per lane.
+// variant: -1 = the handle's choice, 0 / 1 = force 8 / 16 entries per lane;
+// lc: -1 = the handle's choice, 0 / 1 = force column passes / columns across lanes.
 maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,
-                        const int32_t* yperm, cudaStream_t st, int variant = -1);
+                        const int32_t* yperm, cudaStream_t st, int variant = -1, int lc = -1);
 // Time the SpMV variants on this matrix and keep the faster (synchronises).
 maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st);
 
 // batch.cu
 constexpr int64_t kDefaultBatchTask = 2048;  // entries per warp task of the default batch plan
-maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st);
+maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc);
 maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st);
 
 // entropy.cu

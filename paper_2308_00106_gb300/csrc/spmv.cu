@@ -57,6 +57,21 @@ maxe_status launch_variant(const Params& p, cudaStream_t st) {
   return MAXE_OK;
 }
 
+template <typename VT>
+maxe_status launch_lc(const Params& p, int g, cudaStream_t st) {
+  static bool done = false;
+  const size_t smem = sizeof(WarpSmemLC<VT>) * kWarps;
+  if (!done) {
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_lc_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem)));
+    done = true;
+  }
+  const unsigned grid = static_cast<unsigned>(ceil_div(p.nW, kWarps));
+  spmm_lc_kernel<VT><<<grid, kThreads, smem, st>>>(p, g);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  return MAXE_OK;
+}
+
 // it: 0 -> 8 entries per lane, 1 -> 16 (SpMV with unit strides only)
 template <typename VT>
 maxe_status launch_dtype(const Params& p, int vw, int it, bool unit, cudaStream_t st) {
@@ -114,7 +129,7 @@ maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st) {
 }
 
 maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,
-                        const int32_t* yperm, cudaStream_t st, int variant) {
+                        const int32_t* yperm, cudaStream_t st, int variant, int lc) {
   if (h->rows == 0 || k == 0) return MAXE_OK;
   Params p{};
   p.rowptr = h->rowptr;
@@ -146,6 +161,16 @@ maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t 
   if (it == 1 && !unit) return MAXE_ERR_UNSUPPORTED;
   p.wrow = h->wrow[it];
   p.nW = h->nW[it];
+  // k columns across lanes when the rows of X and Y hold whole vectors
+  const int g = lc_group(k, eb, static_cast<int>(ldx % 1024), static_cast<int>(ldy % 1024));
+  const bool use_lc = lc < 0 ? h->spmm_lc != 0 : lc != 0;
+  if (g > 0 && use_lc && aligned(eb == 4 ? 4 : 2)) {
+    switch (h->dtype) {
+      case MAXE_F64: return launch_lc<double>(p, g, st);
+      case MAXE_F32: return launch_lc<float>(p, g, st);
+      case MAXE_BF16: return launch_lc<uint16_t>(p, g, st);
+    }
+  }
   switch (h->dtype) {
     case MAXE_F64: return launch_dtype<double>(p, vw, it, unit, st);
     case MAXE_F32: return launch_dtype<float>(p, vw, it, unit, st);
@@ -165,26 +190,48 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st) {
   cudaEvent_t e0, e1;
   MAXE_CUDA_TRY(cudaEventCreate(&e0));
   MAXE_CUDA_TRY(cudaEventCreate(&e1));
+  // time(launch) over 5 launches after 2 warm-up launches
+  auto timed = [&](auto&& launch, float* ms) -> maxe_status {
+    maxe_status s = MAXE_OK;
+    for (int rep = 0; rep < 2 && s == MAXE_OK; ++rep) s = launch();
+    if (s != MAXE_OK) return s;
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 5 && s == MAXE_OK; ++rep) s = launch();
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return MAXE_ERR_CUDA;
+    cudaEventElapsedTime(ms, e0, e1);
+    return s;
+  };
   float best = 1e30f;
   int pick = 0;
   maxe_status s = MAXE_OK;
   for (int v = 0; v < 2 && s == MAXE_OK; ++v) {
-    for (int rep = 0; rep < 2 && s == MAXE_OK; ++rep) s = spmm_launch(h, 1, x, 1, y, 1, nullptr, st, v);  // warm
-    if (s != MAXE_OK) break;
-    cudaEventRecord(e0, st);
-    for (int rep = 0; rep < 5 && s == MAXE_OK; ++rep) s = spmm_launch(h, 1, x, 1, y, 1, nullptr, st, v);
-    cudaEventRecord(e1, st);
-    if (cudaEventSynchronize(e1) != cudaSuccess) s = MAXE_ERR_CUDA;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    s = timed([&] { return spmm_launch(h, 1, x, 1, y, 1, nullptr, st, v); }, &ms);
     if (s == MAXE_OK && ms < best) {
       best = ms;
       pick = v;
     }
   }
+  h->spmv_items16 = pick;
+  // SpMM path for wide right-hand sides, timed at k = 16 when the scratch is modest
+  const int64_t k = 16;
+  const int64_t bytes = (static_cast<int64_t>(h->rows) + h->cols) * k * eb;
+  if (s == MAXE_OK && bytes <= (int64_t(3) << 30)) {
+    void* X = h->al.get(static_cast<size_t>(h->cols) * k * eb);
+    void* Y = h->al.get(static_cast<size_t>(h->rows) * k * eb);
+    if (X && Y) {
+      s = cudaMemsetAsync(X, 0, static_cast<size_t>(h->cols) * k * eb, st) == cudaSuccess ? MAXE_OK : MAXE_ERR_CUDA;
+      float t_pass = 0.f, t_lc = 0.f;
+      if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 0); }, &t_pass);
+      if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 1); }, &t_lc);
+      if (s == MAXE_OK) h->spmm_lc = t_lc < t_pass ? 1 : 0;
+    }
+    h->al.put(Y);
+    h->al.put(X);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->spmv_items16 = pick;
   return s;
 }
 

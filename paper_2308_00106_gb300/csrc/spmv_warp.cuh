@@ -191,6 +191,10 @@ __device__ __forceinline__ void lds_vals(const uint16_t* p, float (&a)[IT], int 
   }
 }
 
+__device__ __forceinline__ float to_acc_value(float v) { return v; }
+__device__ __forceinline__ double to_acc_value(double v) { return v; }
+__device__ __forceinline__ float to_acc_value(uint16_t v) { return __uint_as_float(static_cast<uint32_t>(v) << 16); }
+
 // Scanned sums of a piece are stored transposed, entry e = IT*lane + j at slot
 // (j*32 + lane): a warp's stores of one j are consecutive (conflict-free).
 template <int IT, int VW>
@@ -421,6 +425,301 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
   gi += static_cast<uint32_t>(npieces);
   __syncwarp();
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// SpMM with lanes over columns (k >= 5 for FP32 values, k >= 3 for FP64).
+//
+// The warp splits into G = 32/g groups of g lanes; lane `sub` of a group owns
+// VC = 4 (FP32) or 2 (FP64) consecutive columns, so a group covers CB = g*VC
+// columns (blocks of CB columns are processed one after the other).  Group q
+// walks its chunk of C = 256/G consecutive entries of the piece in order,
+// accumulating with FMAs: the X row of an entry is one coalesced load per group
+// (one L2 request instead of one per 4 columns), and a row that starts and ends
+// inside the chunk is complete in registers and written at once.  Only the
+// first segment of each chunk (the row running in from the previous chunk) and
+// the tail go through a segmented scan across the G groups (log2 G shuffle
+// steps), as in the single-column kernel.  Rows are found by their end offset
+// (first row of the piece with rowptr[r+1] >= base + o).
+// Ring of the column-lanes kernel: each 32-entry segment of a piece is
+// followed by 16 bytes of padding, so the chunks that the groups read at the
+// same time fall into different shared-memory banks.  (The mbarriers stay at
+// offset 0, as in WarpSmem.)
+template <typename VT>
+struct alignas(16) WarpSmemLC {
+  using AT = typename Acc<VT>::T;
+  static constexpr int kPiece = 256, kSegs = kPiece / 32;
+  static constexpr int kColStride = 32 + 4;                                  // int32 per segment
+  static constexpr int kValStride = 32 + 16 / static_cast<int>(sizeof(VT));  // values per segment
+  uint64_t full[kStages];
+  int32_t col[kStages][kSegs * kColStride];
+  VT val[kStages][kSegs * kValStride];
+  uint32_t flags[kPiece / 32];
+  AT carry[kMaxK + 4];
+  __device__ __forceinline__ int32_t c(int s, int e) const { return col[s][(e >> 5) * kColStride + (e & 31)]; }
+  __device__ __forceinline__ VT v(int s, int e) const { return val[s][(e >> 5) * kValStride + (e & 31)]; }
+};
+
+// One bulk copy per 32-entry segment and array, issued by lanes 0..15.
+template <typename VT>
+__device__ __forceinline__ void issue_piece_lc(WarpSmemLC<VT>& ws, int s, const Params& p, int32_t base,
+                                               uint64_t pol) {
+  using WS = WarpSmemLC<VT>;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_arrive_expect_tx(&ws.full[s], WS::kPiece * (4u + static_cast<uint32_t>(sizeof(VT))));
+  __syncwarp();
+  if (lane < WS::kSegs) {
+    bulk_g2s(&ws.col[s][lane * WS::kColStride], p.col + base + 32 * lane, 32 * 4u, &ws.full[s], pol);
+  } else if (lane < 2 * WS::kSegs) {
+    const int j = lane - WS::kSegs;
+    bulk_g2s(&ws.val[s][j * WS::kValStride], static_cast<const VT*>(p.val) + base + 32 * j,
+             32 * static_cast<uint32_t>(sizeof(VT)), &ws.full[s], pol);
+  }
+}
+
+template <typename VT>
+__device__ __forceinline__ int32_t row_ending_at(const Params& p, int32_t lo, int32_t hi, int32_t target) {
+  while (lo < hi) {  // first row in [lo, hi] whose end >= target
+    const int32_t mid = (lo + hi) >> 1;
+    if (__ldg(p.rowptr + mid + 1) >= target) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+template <typename VT>
+__device__ __forceinline__ bool process_range_lc(const Params& p, int32_t w, unsigned char* wsmem, uint32_t& gi,
+                                                 int g) {
+  using AT = typename Acc<VT>::T;
+  constexpr int IT = 8;
+  constexpr int kPiece = 32 * IT;
+  constexpr int VC = sizeof(AT) == 4 ? 4 : 2;
+  const int lane = threadIdx.x & 31;
+  WarpSmemLC<VT>& ws = *reinterpret_cast<WarpSmemLC<VT>*>(wsmem);
+  const AT* X = static_cast<const AT*>(p.X);
+  AT* Y = static_cast<AT*>(p.Y);
+  const int k = p.k;
+  const int G = 32 / g, C = kPiece / G;
+  const int q = lane / g, sub = lane - q * g;
+  const int CB = g * VC;
+  const int nblocks = (k + CB - 1) / CB;
+
+  const int32_t r_hi = p.wrow[w + 1];
+  int32_t r = p.wrow[w];
+  const int32_t e_lo = p.rowptr[r];
+  const int32_t e_hi = p.rowptr[r_hi];
+  const int32_t base0 = e_lo & ~7;
+  const int32_t npieces = (e_hi > base0) ? (e_hi - base0 + kPiece - 1) / kPiece : 0;
+  const uint64_t pol = policy_evict_first();
+  for (int c = lane; c < nblocks * CB; c += 32) ws.carry[c] = AT(0);
+  if (lane < kPiece / 32) ws.flags[lane] = 0u;
+  __syncwarp();
+  for (int s = 0; s < kStages && s < npieces; ++s)
+    issue_piece_lc(ws, static_cast<int>((gi + s) % kStages), p, base0 + s * kPiece, pol);
+
+  int32_t r_start = e_lo;
+  int32_t end0 = (r + lane < r_hi) ? __ldg(p.rowptr + r + 1 + lane) : INT_MAX;
+
+  for (int32_t i = 0; i < npieces; ++i) {
+    const uint32_t gg = gi + static_cast<uint32_t>(i);
+    const int s = static_cast<int>(gg % kStages);
+    const int32_t base = base0 + i * kPiece;
+    int nend = 0;
+    int32_t last_o = -1;
+    {
+      int32_t end = end0;
+      while (true) {
+        const int32_t o = end - base;
+        const bool in = o <= kPiece;
+        const int n = __popc(__ballot_sync(0xffffffffu, in));
+        if (in && o >= 1 && o < kPiece) atomicOr(&ws.flags[o >> 5], 1u << (o & 31));
+        if (n > 0) last_o = __shfl_sync(0xffffffffu, o, n - 1);
+        nend += n;
+        if (n < 32) break;
+        const int32_t rr = r + nend + lane;
+        end = (rr < r_hi) ? __ldg(p.rowptr + rr + 1) : INT_MAX;
+      }
+    }
+    const int32_t rn = r + nend;
+    const int32_t end_first = end0;
+    end0 = (rn + lane < r_hi) ? __ldg(p.rowptr + rn + 1 + lane) : INT_MAX;
+    __syncwarp();
+    const int e0 = q * C;  // the group's chunk, piece-relative
+    const uint32_t wa = ws.flags[e0 >> 5];
+    const uint32_t wb = ws.flags[min((e0 + C - 1) >> 5, kPiece / 32 - 1)];
+    bool ok = mbar_wait_bounded(&ws.full[s], (gg / kStages) & 1u, p.status);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    __syncwarp();
+    if (lane < kPiece / 32) ws.flags[lane] = 0u;
+    const int32_t rlast = rn - 1;  // rows ending in the piece: [r, rn)
+
+    for (int blk = 0; blk < nblocks; ++blk) {
+      const int cs = blk * CB + sub * VC;  // the lane's first column
+      AT acc[VC], head[VC];
+#pragma unroll
+      for (int u = 0; u < VC; ++u) acc[u] = head[u] = AT(0);
+      bool seen = false;
+      int ffe = 0;           // first row end in the chunk (piece-relative)
+      int32_t rcur = r - 1;  // last row completed inside the chunk
+      for (int i0 = 0; i0 < C; i0 += 8) {
+        AT xv[8][VC];
+        AT av[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + i0 + u;
+          const int32_t ge = base + e;
+          av[u] = AT(0);
+#pragma unroll
+          for (int c = 0; c < VC; ++c) xv[u][c] = AT(0);
+          if (ge >= e_lo && ge < e_hi) {
+            av[u] = to_acc_value(ws.v(s, e));
+            xload<VC>(X, ws.c(s, e), p.ldx, cs, k, xv[u]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + i0 + u;
+          const uint32_t word = ((e >> 5) == (e0 >> 5)) ? wa : wb;
+          if ((word >> (e & 31)) & 1u) {  // a row ends at e: [.., e) is complete
+            if (!seen) {
+              seen = true;
+              ffe = e;
+#pragma unroll
+              for (int c = 0; c < VC; ++c) head[c] = acc[c];
+            } else {
+              int32_t rr = rcur + 1;
+              if (rcur < r) rr = row_ending_at<VT>(p, r, rlast, base + e);
+              while (__ldg(p.rowptr + rr + 1) < base + e) ++rr;  // skip empty rows
+              rcur = rr;
+              const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
+              ystore<VC>(Y, row, p.ldy, cs, k, acc);
+            }
+#pragma unroll
+            for (int c = 0; c < VC; ++c) acc[c] = AT(0);
+          }
+#pragma unroll
+          for (int c = 0; c < VC; ++c) acc[c] = fma(av[u], xv[u][c], acc[c]);
+        }
+      }
+      if (!seen) {
+#pragma unroll
+        for (int c = 0; c < VC; ++c) head[c] = AT(0);
+      }
+      // segmented scan of (seen, tail) across the groups
+      int F = seen;
+      AT V[VC];
+#pragma unroll
+      for (int c = 0; c < VC; ++c) V[c] = acc[c];
+      for (int d = 1; d < G; d <<= 1) {
+        const int Fu = __shfl_up_sync(0xffffffffu, F, d * g);
+        AT Vu[VC];
+#pragma unroll
+        for (int c = 0; c < VC; ++c) Vu[c] = __shfl_up_sync(0xffffffffu, V[c], d * g);
+        if (q >= d) {
+          if (!F)
+#pragma unroll
+            for (int c = 0; c < VC; ++c) V[c] += Vu[c];
+          F |= Fu;
+        }
+      }
+      const int Fe = __shfl_up_sync(0xffffffffu, F, g);
+      AT P[VC], cin[VC];
+#pragma unroll
+      for (int c = 0; c < VC; ++c) {
+        const AT Ve = __shfl_up_sync(0xffffffffu, V[c], g);
+        cin[c] = (cs + c < kMaxK + 4) ? ws.carry[cs + c] : AT(0);
+        P[c] = (q == 0) ? cin[c] : (Fe ? Ve : cin[c] + Ve);
+      }
+      if (seen) {  // the row running into the chunk ends at its first row end
+        const int32_t rr = row_ending_at<VT>(p, r, rlast, base + ffe);
+        AT out[VC];
+#pragma unroll
+        for (int c = 0; c < VC; ++c) out[c] = P[c] + head[c];
+        const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
+        ystore<VC>(Y, row, p.ldy, cs, k, out);
+      }
+      // inclusive value of the last group, per column of this lane
+      const int src = (G - 1) * g + sub;
+      const int Fl = __shfl_sync(0xffffffffu, F, src);
+      AT inc[VC];
+#pragma unroll
+      for (int c = 0; c < VC; ++c) {
+        const AT Vl = __shfl_sync(0xffffffffu, V[c], src);
+        inc[c] = Fl ? Vl : cin[c] + Vl;
+      }
+      __syncwarp();
+      if (last_o == kPiece) {  // a row ends exactly at the end of the piece
+        if (q == G - 1) {
+          const int32_t rr = row_ending_at<VT>(p, r, rlast, base + kPiece);
+          const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
+          ystore<VC>(Y, row, p.ldy, cs, k, inc);
+        }
+        if (q == 0)
+#pragma unroll
+          for (int c = 0; c < VC; ++c)
+            if (cs + c < kMaxK + 4) ws.carry[cs + c] = AT(0);
+      } else if (q == 0) {
+#pragma unroll
+        for (int c = 0; c < VC; ++c)
+          if (cs + c < kMaxK + 4) ws.carry[cs + c] = inc[c];
+      }
+      __syncwarp();
+    }
+    // empty rows of the piece get zeros
+    int32_t prev_end = r_start;
+    for (int b = 0; b < nend; b += 32) {
+      const int32_t rr = r + b + lane;
+      int32_t end = end_first;
+      if (b > 0) end = (rr < r_hi) ? __ldg(p.rowptr + rr + 1) : INT_MAX;
+      int32_t start = __shfl_up_sync(0xffffffffu, end, 1);
+      if (lane == 0) start = prev_end;
+      if (b + lane < nend && end == start) {
+        const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
+        for (int c = 0; c < k; ++c) Y[row * p.ldy + c] = AT(0);
+      }
+      prev_end = __shfl_sync(0xffffffffu, end, 31);
+    }
+    if (nend > 0) r_start = base + last_o;
+    r = rn;
+    // the stage has been read: refill it with piece i + kStages
+    __syncwarp();
+    if (i + kStages < npieces) {
+      fence_proxy_async_smem();
+      issue_piece_lc(ws, s, p, base + kStages * kPiece, pol);
+    }
+  }
+  for (int32_t rr = r + lane; rr < r_hi; rr += 32) {
+    const int64_t row = p.yperm ? static_cast<int64_t>(p.yperm[rr]) : static_cast<int64_t>(rr);
+    for (int c = 0; c < k; ++c) Y[row * p.ldy + c] = AT(0);
+  }
+  gi += static_cast<uint32_t>(npieces);
+  __syncwarp();
+  return true;
+}
+
+// groups of g lanes for k columns (0: use the column-pass kernel instead)
+__host__ __device__ inline int lc_group(int k, int value_bytes_acc, int ldx, int ldy) {
+  const int vc = value_bytes_acc == 4 ? 4 : 2;
+  if (k < (vc == 4 ? 5 : 3) || ldx % vc != 0 || ldy % vc != 0) return 0;
+  if (k <= 2 * vc) return 2;
+  if (k <= 4 * vc) return 4;
+  return 8;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads, 2) spmm_lc_kernel(Params p, int g) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarps + wib;
+  if (w >= p.nW) return;
+  unsigned char* wsmem = smem_raw + sizeof(WarpSmemLC<VT>) * wib;
+  WarpSmemLC<VT>& ws = *reinterpret_cast<WarpSmemLC<VT>*>(wsmem);
+  if ((threadIdx.x & 31) == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&ws.full[s], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t gi = 0;
+  process_range_lc<VT>(p, w, wsmem, gi, g);
 }
 
 template <class C>

@@ -25,6 +25,7 @@ MAXE_VEC_PERMUTED = 0x1
 MAXE_VALIDATE = 0x2
 MAXE_AUTOTUNE = 0x4
 MAXE_ITEMS16 = 0x8
+MAXE_SPMM_LANES = 0x10
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -213,6 +214,13 @@ class Handle:
 
     def items_per_lane(self) -> int:
         """Entries per lane of the SpMV kernel variant this handle uses (8 or 16)."""
+        return self._tuning() & 0xFF
+
+    def spmm_lanes(self) -> bool:
+        """True when SpMM spreads the k columns across lanes (else column passes)."""
+        return bool(self._tuning() & 0x100)
+
+    def _tuning(self) -> int:
         v = ctypes.c_int32()
         _check(load().maxe_handle_tuning(ctypes.c_void_p(self.ptr), ctypes.byref(v)), "maxe_handle_tuning")
         return v.value
@@ -270,7 +278,7 @@ def maxe_permute_scatter(perm: torch.Tensor, y: torch.Tensor, stream=None):
 
 def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
-                     stream=None, autotune: bool = False, items16: bool = False) -> Handle:
+                     stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False) -> Handle:
     """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity."""
     code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[val.dtype]
     _dev(rowptr, torch.int32, "rowptr")
@@ -283,7 +291,8 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
     A = _Csr(rows, cols, col.numel(), rowptr.data_ptr(), col.data_ptr() if col.numel() else None,
              val.data_ptr() if val.numel() else None, code)
     out = ctypes.c_void_p()
-    flags = (MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
+    flags = ((MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
+             | (MAXE_SPMM_LANES if spmm_lanes else 0))
     _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
@@ -346,9 +355,11 @@ def maxe_version() -> str:
     return load().maxe_version().decode()
 
 
-def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False) -> Handle:
+def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False,
+             spmm_lanes=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
-    return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16)
+    return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16,
+                            spmm_lanes)
 
 
 class Batch:

@@ -38,9 +38,12 @@ def _setup(mats, ks, seed=1):
     for i, (A, k) in enumerate(zip(mats, ks)):
         r = maxe.maxe_build_permutation(seed + i, A.rows, 0)
         c = maxe.maxe_build_permutation(seed + i, A.cols, 1)
-        h = maxe.from_csr(A.to("cuda"), r, c)
-        X = W.matrix_rhs(100 + i, A.cols, k, "f64" if A.dtype == "f64" else "f32", "cuda")
-        items.append((A, h, r, c, X))
+        # odd items use the columns-across-lanes SpMM path: one launch mixes both
+        h = maxe.from_csr(A.to("cuda"), r, c, spmm_lanes=bool(i % 2))
+        kp = (k + 3) // 4 * 4 if k > 1 else 1
+        Xb = torch.zeros(A.cols, kp, dtype=torch.float64 if A.dtype == "f64" else torch.float32, device="cuda")
+        Xb[:, :k] = W.matrix_rhs(100 + i, A.cols, k, "f64" if A.dtype == "f64" else "f32", "cuda")
+        items.append((A, h, r, c, Xb[:, :k]))
     return items
 
 
@@ -64,7 +67,8 @@ def test_batch_matches_oracle_per_item(scatter):
     mats = _mats()
     items = _setup(mats, KS)
     b = maxe.Batch(len(items))
-    Ys = [torch.full((A.rows, X.shape[1]), float("nan"), dtype=X.dtype, device="cuda") for A, h, r, c, X in items]
+    Ys = [torch.full((A.rows, X.stride(0)), float("nan"), dtype=X.dtype, device="cuda")[:, :X.shape[1]]
+          for A, h, r, c, X in items]
     b.set([(h, X, Y, scatter) for (A, h, r, c, X), Y in zip(items, Ys)])
     b.run()
     torch.cuda.synchronize()
@@ -76,15 +80,15 @@ def test_batch_item_alone_equals_in_mix_bitwise():
     mats = _mats()
     items = _setup(mats, KS, seed=7)
     b = maxe.Batch(len(items))
-    Ymix = [torch.empty((A.rows, X.shape[1]), dtype=X.dtype, device="cuda") for A, h, r, c, X in items]
+    Ymix = [torch.empty((A.rows, X.stride(0)), dtype=X.dtype, device="cuda")[:, :X.shape[1]] for A, h, r, c, X in items]
     b.set([(h, X, Y, False) for (A, h, r, c, X), Y in zip(items, Ymix)])
     b.run()
     order = list(range(len(items)))[::-1]
-    Yrev = [torch.empty_like(y) for y in Ymix]
+    Yrev = [torch.empty((y.shape[0], y.stride(0)), dtype=y.dtype, device="cuda")[:, :y.shape[1]] for y in Ymix]
     b.set([(items[i][1], items[i][4], Yrev[i], False) for i in order])  # same items, another order
     b.run()
     for i, (A, h, r, c, X) in enumerate(items):
-        Yalone = torch.empty_like(Ymix[i])
+        Yalone = torch.empty((A.rows, X.stride(0)), dtype=X.dtype, device="cuda")[:, :X.shape[1]]
         b1 = maxe.Batch(1)
         b1.set([(h, X, Yalone, False)])
         b1.run()
