@@ -10,6 +10,8 @@ Each wrapper names the passage of the paper it states:
   build_permutation / invert_permutation / gather / scatter  -- Section 3 and Eq. 1
   permute_csr                                                  -- Eq. 1 on CSR (Section 2)
   nnz_entropy                                                  -- Section 4, entropy equation
+  entropy_levels                                               -- Section 5, hierarchical 2-D entropy
+  nnz_histogram / gradient_permutation                         -- Section 5 and appendix, gradient shuffles
   spmv / spmm / spmv_rows                                      -- Section 2, CSR product
   power_iteration                                              -- not in the paper (serving reference)
 
@@ -65,6 +67,9 @@ def _load():
             lib.orc_nnz_entropy.restype = ctypes.c_double
             lib.orc_nnz_entropy.argtypes = [_I32, _I32, _P, _P, _I32, _I32, ctypes.c_double, _P]
             lib.orc_spmv.argtypes = [_I32, _P, _P, _P, ctypes.c_int, _P, _P]
+            lib.orc_entropy_levels.argtypes = [_P, _I32, _I32, _I32, ctypes.c_double, _P]
+            lib.orc_nnz_histogram.argtypes = [_I32, _I32, _P, _P, _I32, _P]
+            lib.orc_gradient_permutation.argtypes = [_P, _I32, ctypes.c_uint64, _I32, _P, _P]
             lib.orc_spmm.argtypes = [_I32, _P, _P, _P, ctypes.c_int, _I32, _P, _I64, _P, _I64]
             lib.orc_spmv_rows.argtypes = [_P, _P, _P, ctypes.c_int, _P, _P, _I64, _P]
             lib.orc_power_iteration.restype = ctypes.c_double
@@ -155,6 +160,37 @@ def nnz_entropy(M: int, N: int, rowptr, col, gr: int, gc: int, base: float = 2.0
     counts = np.empty(gr * gc, dtype=np.int64)
     H = _load().orc_nnz_entropy(M, N, _ptr(rowptr), _ptr(col), gr, gc, float(base), _ptr(counts))
     return float(H), counts.reshape(gr, gc)
+
+
+def entropy_levels(counts, L: int, base: float = 2.0) -> np.ndarray:
+    """L x L map of block entropies of a (gr, gc) count grid (Section 5, hierarchical 2-D entropy)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    gr, gc = counts.shape
+    if not (1 <= L <= gr and L <= gc):
+        raise ValueError("need 1 <= L <= gr, gc")
+    out = np.empty(L * L, dtype=np.float64)
+    _load().orc_entropy_levels(_ptr(counts), gr, gc, L, float(base), _ptr(out))
+    return out.reshape(L, L)
+
+
+def nnz_histogram(M: int, N: int, rowptr, col, axis: int) -> np.ndarray:
+    """Entries per row (axis 0) or per column (axis 1) (Section 5, appendix)."""
+    rowptr, col = _i32(rowptr), _i32(col)
+    h = np.empty(M if axis == 0 else N, dtype=np.int32)
+    _load().orc_nnz_histogram(M, N, _ptr(rowptr), _ptr(col), int(axis), _ptr(h))
+    return h
+
+
+def gradient_permutation(hist, seed: int, tag: int):
+    """(perm, pivot): cut at the steepest histogram gradient, riffle, permute each
+    half of the shuffled deck at random (appendix, gradient-based permutations)."""
+    hist = _i32(hist)
+    perm = np.empty(hist.size, dtype=np.int32)
+    pivot = ctypes.c_int32(-1)
+    if _load().orc_gradient_permutation(_ptr(hist), hist.size, seed & (2**64 - 1), tag, _ptr(perm),
+                                        ctypes.byref(pivot)) != 0:
+        raise ValueError("gradient_permutation failed")
+    return perm, int(pivot.value)
 
 
 def spmv(M: int, rowptr, col, val, dtype: int, x) -> np.ndarray:

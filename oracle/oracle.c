@@ -206,6 +206,114 @@ double orc_nnz_entropy(int32_t M, int32_t N, const int32_t* rowptr, const int32_
   return H;
 }
 
+/* Hierarchical 2-D entropy (Section 5: the entropy "split into 2x2, 4x4 and
+ * 8x8"): the gr x gc count grid is cut into L x L blocks, block (a, b) taking
+ * grid rows [ceil(a*gr/L), ceil((a+1)*gr/L)) and grid columns likewise; out[a*L+b]
+ * is the entropy of the counts inside that block (0 for an empty block).
+ * Requires 1 <= L <= gr, L <= gc. */
+void orc_entropy_levels(const int64_t* counts, int32_t gr, int32_t gc, int32_t L, double base, double* out) {
+  for (int32_t a = 0; a < L; ++a) {
+    int64_t r0 = ((int64_t)a * gr + L - 1) / L, r1 = ((int64_t)(a + 1) * gr + L - 1) / L;
+    for (int32_t b = 0; b < L; ++b) {
+      int64_t c0 = ((int64_t)b * gc + L - 1) / L, c1 = ((int64_t)(b + 1) * gc + L - 1) / L;
+      int64_t S = 0;
+      for (int64_t i = r0; i < r1; ++i)
+        for (int64_t j = c0; j < c1; ++j) S += counts[i * gc + j];
+      double H = 0.0;
+      if (S > 0) {
+        for (int64_t i = r0; i < r1; ++i)
+          for (int64_t j = c0; j < c1; ++j) {
+            int64_t c = counts[i * gc + j];
+            if (c == 0) continue;
+            double p = (double)c / (double)S;
+            H -= p * ((base == 2.0) ? log2(p) : log(p) / log(base));
+          }
+      }
+      out[a * L + b] = H;
+    }
+  }
+}
+
+/* ---------------------------- gradient-based permutations (Section 5, appendix) */
+
+/* Nonzero histogram along one axis: axis 0 gives the entries of each row
+ * (M values), axis 1 the entries of each column (N values). */
+void orc_nnz_histogram(int32_t M, int32_t N, const int32_t* rowptr, const int32_t* col, int32_t axis,
+                       int32_t* hist) {
+  if (axis == 0) {
+    for (int32_t i = 0; i < M; ++i) hist[i] = rowptr[i + 1] - rowptr[i];
+  } else {
+    for (int32_t j = 0; j < N; ++j) hist[j] = 0;
+    for (int64_t e = 0; e < (int64_t)rowptr[M]; ++e) hist[col[e]] += 1;
+  }
+}
+
+/* Gradient-based permutation of n rows (or columns) from their histogram h.
+ * Steps, in the paper's order:
+ *   1. gradient g_i = h_{i+1} - h_i, i = 0..n-2;
+ *   2. the pivot is the point of maximum steepness, max |g_i| (the first i on
+ *      ties); the deck is cut before element i+1, so part one is [0, pivot) and
+ *      part two [pivot, n), pivot = i+1 (pivot = n when n < 2: one part);
+ *   3. riffle: cards are taken alternately from the top of part one and part
+ *      two, starting with part one; when one part runs out the rest of the
+ *      other follows in order;
+ *   4. the shuffled deck is split into two parts again, its first ceil(n/2)
+ *      cards and the rest, and each part is permuted at random: the positions
+ *      q of a part are ordered by (key(seed, tag, q), q), the key of the
+ *      Section 3 permutation.
+ * perm[new] = old, as everywhere.  *pivot_out receives the cut (may be NULL). */
+int orc_gradient_permutation(const int32_t* h, int32_t n, uint64_t seed, int32_t tag, int32_t* perm,
+                             int32_t* pivot_out) {
+  if (n < 0) return -1;
+  int32_t pivot = n;
+  if (n >= 2) {
+    int64_t best = -1;
+    for (int32_t i = 0; i + 1 < n; ++i) {
+      int64_t g = (int64_t)h[i + 1] - (int64_t)h[i];
+      int64_t steep = g < 0 ? -g : g;
+      if (steep > best) {
+        best = steep;
+        pivot = i + 1;
+      }
+    }
+  }
+  if (pivot_out) *pivot_out = pivot;
+  if (n == 0) return 0;
+  int32_t* deck = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  orc_pair* pr = (orc_pair*)malloc(sizeof(orc_pair) * (size_t)n);
+  if (!deck || !pr) {
+    free(deck);
+    free(pr);
+    return -2;
+  }
+  /* 3. the riffle, card by card */
+  int32_t top1 = 0, top2 = pivot, out = 0;
+  int take_one = 1;
+  while (out < n) {
+    if (top1 < pivot && (take_one || top2 >= n)) {
+      deck[out++] = top1++;
+    } else {
+      deck[out++] = top2++;
+    }
+    take_one = !take_one;
+  }
+  /* 4. random permutation inside each part of the shuffled deck */
+  int32_t half = (n + 1) / 2;
+  int32_t bounds[3] = {0, half, n};
+  for (int part = 0; part < 2; ++part) {
+    int32_t s = bounds[part], e = bounds[part + 1];
+    for (int32_t q = s; q < e; ++q) {
+      pr[q - s].key = orc_key(seed, tag, q);
+      pr[q - s].idx = q;
+    }
+    qsort(pr, (size_t)(e - s), sizeof(orc_pair), orc_pair_cmp);
+    for (int32_t t = 0; t < e - s; ++t) perm[s + t] = deck[pr[t].idx];
+  }
+  free(deck);
+  free(pr);
+  return 0;
+}
+
 /* ----------------------------------------------------- SpMV (Section 2) */
 
 /* y_i = sum_{l in ROW[i]:ROW[i+1]} V[l] * x[COL[l]], in stored order, FP64. */

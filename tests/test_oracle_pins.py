@@ -293,6 +293,162 @@ def test_entropy_rejects_bad_grid():
         oracle.nnz_entropy(4, 4, np.zeros(5, np.int32), np.zeros(0, np.int32), 5, 1)
 
 
+# ------------------------------------------- hierarchical 2-D entropy (Section 5)
+
+def test_entropy_levels_one_block_is_global_entropy():
+    A = small_csr(31, 40, 36, "f64", density=0.4)
+    rp, co, va = A.numpy()
+    H, cnt = oracle.nnz_entropy(40, 36, rp, co, 8, 6)
+    lv = oracle.entropy_levels(cnt, 1)
+    assert lv.shape == (1, 1) and lv[0, 0] == pytest.approx(H, rel=1e-14)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4, 8])
+def test_entropy_levels_uniform_counts_are_log2_cells(L):
+    counts = np.full((16, 16), 3, dtype=np.int64)
+    lv = oracle.entropy_levels(counts, L)
+    assert np.all(lv == math.log2((16 // L) ** 2))  # exact: power-of-two cells per block
+
+
+def test_entropy_levels_single_cell_and_empty_blocks_are_zero():
+    counts = np.zeros((8, 8), dtype=np.int64)
+    counts[0, 0] = 7  # block (0, 0) of a 2 x 2 split holds one nonzero cell
+    counts[6, 1] = 2
+    counts[7, 2] = 2  # block (1, 0): two equal cells -> 1 bit
+    lv = oracle.entropy_levels(counts, 2)
+    assert lv[0, 0] == 0.0 and lv[0, 1] == 0.0 and lv[1, 1] == 0.0
+    assert lv[1, 0] == 1.0
+
+
+@pytest.mark.parametrize("shape,L", [((13, 11), 3), ((32, 32), 4), ((9, 20), 9), ((64, 48), 8)])
+def test_entropy_levels_match_scipy_on_numpy_blocks(shape, L):
+    g = np.random.default_rng(shape[0] * 100 + L)
+    counts = g.integers(0, 5, size=shape).astype(np.int64)
+    counts[g.random(shape) < 0.3] = 0
+    lv = oracle.entropy_levels(counts, L)
+    gr, gc = shape
+    re = [-(-a * gr // L) for a in range(L + 1)]
+    ce = [-(-b * gc // L) for b in range(L + 1)]
+    for a in range(L):
+        for b in range(L):
+            blk = counts[re[a]:re[a + 1], ce[b]:ce[b + 1]].ravel()
+            want = scipy.stats.entropy(blk, base=2) if blk.sum() else 0.0
+            assert lv[a, b] == pytest.approx(want, rel=1e-13, abs=1e-15)
+
+
+@pytest.mark.parametrize("L", [2, 3, 5])
+def test_entropy_levels_chain_rule(L):
+    """H(cells) = H(blocks) + sum_b P(b) H(cells | b): the map and the block totals
+    must recompose the global entropy, whatever the block edges."""
+    g = np.random.default_rng(L)
+    counts = g.integers(0, 9, size=(20, 15)).astype(np.int64)
+    lv = oracle.entropy_levels(counts, L)
+    Hg = oracle.entropy_levels(counts, 1)[0, 0]
+    # block totals from the oracle's own edges, reconstructed as those of the L-split
+    re = [-(-a * 20 // L) for a in range(L + 1)]
+    ce = [-(-b * 15 // L) for b in range(L + 1)]
+    tot = np.array([[counts[re[a]:re[a + 1], ce[b]:ce[b + 1]].sum() for b in range(L)] for a in range(L)], float)
+    P = tot / tot.sum()
+    Hb = scipy.stats.entropy(P.ravel(), base=2)
+    assert Hg == pytest.approx(Hb + float((P * lv).sum()), rel=1e-13)
+
+
+def test_entropy_levels_rejects_bad_split():
+    with pytest.raises(ValueError):
+        oracle.entropy_levels(np.ones((4, 4), np.int64), 5)
+    with pytest.raises(ValueError):
+        oracle.entropy_levels(np.ones((4, 4), np.int64), 0)
+
+
+# ------------------------------- gradient-based permutations (Section 5, appendix)
+
+def test_nnz_histogram_rows_and_columns():
+    A = small_csr(41, 33, 27, "f64", density=0.35)
+    rp, co, _ = A.numpy()
+    np.testing.assert_array_equal(oracle.nnz_histogram(33, 27, rp, co, 0), np.diff(rp))
+    np.testing.assert_array_equal(oracle.nnz_histogram(33, 27, rp, co, 1), np.bincount(co, minlength=27))
+
+
+def _deck_from_perm(perm, seed, tag):
+    """Undo the per-half random order with numpy's sort of the published
+    SplitMix64 keys: deck[q] = perm[s + rank of q inside its half]."""
+    n = perm.size
+    half = (n + 1) // 2
+    deck = np.empty(n, dtype=np.int64)
+    for s, e in ((0, half), (half, n)):
+        q = np.arange(s, e)
+        keys = np.array([oracle.key(seed, tag, int(i)) for i in q], dtype=np.uint64)
+        order = q[np.lexsort((q, keys))]  # positions sorted by (key, position)
+        deck[order] = perm[s:e]
+    return deck
+
+
+@pytest.mark.parametrize("seed", [0, 5, 2**63 + 11])
+def test_gradient_pivot_is_first_steepest_step(seed):
+    g = np.random.default_rng(seed % 1000)
+    for n in (2, 3, 17, 100, 501):
+        h = g.integers(0, 4, n)  # small range: many tied gradients
+        perm, pivot = oracle.gradient_permutation(h, seed, 0)
+        assert pivot == int(np.argmax(np.abs(np.diff(h)))) + 1  # numpy argmax: first maximum
+        assert np.array_equal(np.sort(perm), np.arange(n))
+
+
+def test_gradient_riffle_at_middle_is_the_out_faro_shuffle():
+    """A cut at n/2 makes the riffle a perfect out-shuffle (top card stays on
+    top); eight out-shuffles restore a 52-card deck, a textbook fact."""
+    h = np.array([7] * 26 + [2] * 26)
+    for seed in (1, 2, 3):
+        perm, pivot = oracle.gradient_permutation(h, seed, 1)
+        assert pivot == 26
+        deck = _deck_from_perm(perm, seed, 1)
+        np.testing.assert_array_equal(deck[0::2], np.arange(26))
+        np.testing.assert_array_equal(deck[1::2], np.arange(26, 52))
+        p = np.arange(52)
+        for r in range(1, 9):
+            p = p[deck]
+            assert np.array_equal(p, np.arange(52)) == (r == 8)  # order exactly 8
+
+
+@pytest.mark.parametrize("n,cut", [(10, 3), (10, 7), (9, 1), (9, 8), (1000, 13), (1001, 990)])
+def test_gradient_riffle_with_unequal_parts(n, cut):
+    """Alternate cards while both parts last, then the longer part's remainder in order."""
+    h = np.zeros(n, dtype=np.int64)
+    h[:cut] = 50  # one step, at the cut
+    perm, pivot = oracle.gradient_permutation(h, 77, 0)
+    assert pivot == cut
+    deck = _deck_from_perm(perm, 77, 0)
+    m = min(cut, n - cut)
+    np.testing.assert_array_equal(deck[0:2 * m:2], np.arange(m))
+    np.testing.assert_array_equal(deck[1:2 * m:2], cut + np.arange(m))
+    rest = np.arange(m, cut) if cut > n - cut else np.arange(cut + m, n)
+    np.testing.assert_array_equal(deck[2 * m:], rest)
+
+
+def test_gradient_degenerate_sizes_and_flat_histogram():
+    assert oracle.gradient_permutation([], 3, 0)[0].size == 0
+    perm, pivot = oracle.gradient_permutation([4], 3, 0)
+    assert perm.tolist() == [0] and pivot == 1
+    perm, pivot = oracle.gradient_permutation([2, 9], 3, 0)
+    assert pivot == 1 and perm.tolist() == [0, 1]  # deck [0, 1], halves of one card each
+    perm, pivot = oracle.gradient_permutation(np.full(40, 6), 3, 0)
+    assert pivot == 1  # flat: every gradient ties at 0, the first wins
+
+
+def test_gradient_halves_are_uniformly_permuted():
+    """Each card of a half lands on each position of the half equally often over seeds."""
+    n, trials = 8, 4000
+    h = np.array([9, 9, 9, 9, 1, 1, 1, 1])
+    pos = np.zeros((n, n))
+    for seed in range(trials):
+        perm, _ = oracle.gradient_permutation(h, seed, 0)
+        pos[perm, np.arange(n)] += 1
+    # cards of the first half of the deck [0, 4, 1, 5] stay in positions 0..3
+    for card in (0, 4, 1, 5):
+        assert pos[card, 4:].sum() == 0
+        chi2 = ((pos[card, :4] - trials / 4) ** 2 / (trials / 4)).sum()
+        assert chi2 < 16.3  # 3 d.o.f., p ~ 0.001
+
+
 # ------------------------------------------------------------ power iteration
 
 def test_power_iteration_diagonal_closed_form():
