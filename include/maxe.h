@@ -76,6 +76,11 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * for k >= 5 (FP32 vectors) / k >= 3 (FP64) with 16-byte rows of X and Y
  * (tuning override; MAXE_AUTOTUNE takes precedence). */
 #define MAXE_SPMM_LANES 0x10u
+/* Flag of maxe_permute_csr: split the SpMV work into equal numbers of rows
+ * per warp instead of equal numbers of nonzeros.  This is the fixed row
+ * partition under which the paper finds that random permutation balances the
+ * load (Section 6, parallel CSR and GPU CSR by equal rows). */
+#define MAXE_EQUAL_ROWS 0x20u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -131,7 +136,8 @@ MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_
  * cinv[c]; each row is then sorted by new column (stable).  Values are copied
  * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
  * (the "plain" matrix).  The handle keeps its own copies of the permutations.
- * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16, MAXE_SPMM_LANES.  *out receives the new handle.
+ * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16, MAXE_SPMM_LANES,
+ * MAXE_EQUAL_ROWS.  *out receives the new handle.
  * Synchronises `stream` once (to size the pass over rows longer than 2048).
  * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
 MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
@@ -158,6 +164,16 @@ MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
  * alloc: scratch allocator (nullable).  Synchronises `stream`. */
 MAXE_API maxe_status maxe_nnz_entropy(const maxe_handle* h, int32_t gr, int32_t gc, double base, double* H_host,
                              int64_t* counts_dev, const maxe_allocator* alloc, void* stream);
+
+/* Hierarchical 2-D entropy map (Section 5: the entropy split into 2x2, 4x4
+ * and 8x8 blocks).  The gr x gc count grid (from maxe_nnz_entropy) is cut into
+ * L x L blocks, block (a, b) holding grid rows [ceil(a*gr/L), ceil((a+1)*gr/L))
+ * and grid columns likewise; H_dev[a*L + b] is the entropy (in `base`) of the
+ * counts inside the block, 0 for an empty block.  counts_dev: (device) int64
+ * [gr*gc]; H_dev: (device) double [L*L].  1 <= L <= min(gr, gc, 4096).
+ * Stream-ordered, no synchronisation; deterministic. */
+MAXE_API maxe_status maxe_entropy_levels(const int64_t* counts_dev, int32_t gr, int32_t gc, int32_t L, double base,
+                                         double* H_dev, void* stream);
 
 /* Allocation-free form of maxe_nnz_entropy (the paper has no counterpart).
  * Some callers cannot call cudaMalloc: for example a host framework that has

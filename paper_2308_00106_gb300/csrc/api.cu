@@ -127,7 +127,8 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (bad_size(A->rows) || bad_size(A->cols) || bad_size(A->nnz) || bad_dtype(A->dtype)) return MAXE_ERR_INVALID;
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return MAXE_ERR_INVALID;
   if (A->nnz > 0 && (A->rows == 0 || A->cols == 0)) return MAXE_ERR_INVALID;
-  if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16 | MAXE_SPMM_LANES))
+  if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16 | MAXE_SPMM_LANES |
+                                     MAXE_EQUAL_ROWS))
     return MAXE_ERR_INVALID;
   DeviceInfo di{};
   MAXE_TRY(device_info(&di));
@@ -142,6 +143,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   h->device = di.device;
   h->sms = di.sms;
   h->status = di.status;
+  h->equal_rows = (flags & MAXE_EQUAL_ROWS) ? 1 : 0;
   maxe_status s = permute_csr_run(A, rperm, cperm, flags, h, st);
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
   if (s == MAXE_OK) s = batch_plan_default(h, st);

@@ -121,6 +121,48 @@ __global__ void __launch_bounds__(kEThreads) entropy_kernel(const unsigned* __re
   }
 }
 
+// Hierarchical 2-D entropy: one CTA per cell (a, b) of an L x L split of the
+// count grid; the cell's total, then -sum p log p, both reduced in a fixed order.
+constexpr int kLThreads = 256;
+
+__global__ void __launch_bounds__(kLThreads) entropy_levels_kernel(const int64_t* __restrict__ counts, int32_t gr,
+                                                                   int32_t gc, int32_t L, double base,
+                                                                   double* __restrict__ out) {
+  __shared__ double ws[kLThreads / 32];
+  __shared__ long long wt[kLThreads / 32];
+  const int a = blockIdx.x / L, b = blockIdx.x - (blockIdx.x / L) * L;
+  const int64_t r0 = (static_cast<int64_t>(a) * gr + L - 1) / L, r1 = (static_cast<int64_t>(a + 1) * gr + L - 1) / L;
+  const int64_t c0 = (static_cast<int64_t>(b) * gc + L - 1) / L, c1 = (static_cast<int64_t>(b + 1) * gc + L - 1) / L;
+  const int64_t w = c1 - c0, n = (r1 - r0) * w;
+  long long t = 0;
+  for (int64_t i = threadIdx.x; i < n; i += kLThreads) t += counts[(r0 + i / w) * gc + c0 + i % w];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+  if ((threadIdx.x & 31) == 0) wt[threadIdx.x >> 5] = t;
+  __syncthreads();
+  long long S = 0;
+  for (int k = 0; k < kLThreads / 32; ++k) S += wt[k];
+  double acc = 0.0;
+  if (S > 0) {
+    const double inv_lb = (base == 2.0) ? 1.0 : 1.0 / log(base);
+    for (int64_t i = threadIdx.x; i < n; i += kLThreads) {
+      const long long c = counts[(r0 + i / w) * gc + c0 + i % w];
+      if (c == 0) continue;
+      const double pr = static_cast<double>(c) / static_cast<double>(S);
+      acc -= pr * ((base == 2.0) ? log2(pr) : log(pr) * inv_lb);
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double H = 0.0;
+    for (int k = 0; k < kLThreads / 32; ++k) H += ws[k];
+    out[blockIdx.x] = H;
+  }
+}
+
 }  // namespace
 
 maxe_status entropy_run(const maxe_handle* h, int32_t gr, int32_t gc, double base, double* H_host,
@@ -145,6 +187,17 @@ maxe_status entropy_run(const maxe_handle* h, int32_t gr, int32_t gc, double bas
 }
 
 }  // namespace maxe
+
+extern "C" maxe_status maxe_entropy_levels(const int64_t* counts_dev, int32_t gr, int32_t gc, int32_t L, double base,
+                                           double* H_dev, void* stream) {
+  using namespace maxe;
+  if (!counts_dev || !H_dev || gr < 1 || gc < 1 || L < 1 || L > gr || L > gc || !(base > 1.0) || L > 4096)
+    return MAXE_ERR_INVALID;
+  entropy_levels_kernel<<<static_cast<unsigned>(L) * L, kLThreads, 0, as_stream(stream)>>>(counts_dev, gr, gc, L,
+                                                                                             base, H_dev);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  return MAXE_OK;
+}
 
 // ------------------------------------------------- allocation-free variant
 namespace {

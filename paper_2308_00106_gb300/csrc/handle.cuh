@@ -27,6 +27,7 @@ struct maxe_handle {
   int32_t nW[2] = {0, 0};
   int spmv_items16 = 0;                    // chosen SpMV variant (autotuned or 0)
   int spmm_lc = 0;                         // SpMM with columns across lanes (autotuned or 0)
+  int equal_rows = 0;                      // SpMV partition: equal rows per warp (not equal nonzeros)
   int32_t* bwrow = nullptr;                // batch plan: partition with bH entries per warp task
   int32_t bnW = 0;
   int64_t bH = 0;

@@ -113,9 +113,28 @@ int resident_for(maxe_dtype d, int sms) {
 
 int64_t spmv_pad_elems() { return 32 * kMaxItems * kStages + 8; }
 
+namespace {
+
+// wrow[w] = w * M / nW: the same number of rows for every warp, whatever they hold.
+__global__ void equal_rows_kernel(int32_t* __restrict__ wrow, int64_t nW, int64_t M) {
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w <= nW) wrow[w] = static_cast<int32_t>(w * M / nW);
+}
+
+}  // namespace
+
 maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st) {
   for (int v = 0; v < 2; ++v) {
     const int target = v == 0 ? resident_for<8>(h->dtype, h->sms) : resident_for<16>(h->dtype, h->sms);
+    if (h->equal_rows) {
+      const int64_t nW = std::max<int64_t>(1, std::min<int64_t>(target, h->rows));
+      h->wrow[v] = static_cast<int32_t*>(h->al.get(static_cast<size_t>(nW + 1) * sizeof(int32_t)));
+      if (!h->wrow[v]) return MAXE_ERR_OOM;
+      h->nW[v] = static_cast<int32_t>(nW);
+      equal_rows_kernel<<<static_cast<unsigned>(ceil_div(nW + 1, 256)), 256, 0, st>>>(h->wrow[v], nW, h->rows);
+      MAXE_CUDA_TRY(cudaGetLastError());
+      continue;
+    }
     const int64_t H = std::max<int64_t>(256, ceil_div(std::max<int64_t>(h->nnz, 1), std::max(target, 1)));
     const int64_t nW = std::max<int64_t>(1, ceil_div(h->nnz, H));
     h->wrow[v] = static_cast<int32_t*>(h->al.get(static_cast<size_t>(nW + 1) * sizeof(int32_t)));

@@ -26,6 +26,7 @@ MAXE_VALIDATE = 0x2
 MAXE_AUTOTUNE = 0x4
 MAXE_ITEMS16 = 0x8
 MAXE_SPMM_LANES = 0x10
+MAXE_EQUAL_ROWS = 0x20
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -36,7 +37,7 @@ EXPORTS = [
     "maxe_permute_csr", "maxe_handle_csr", "maxe_handle_tuning", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmm", "maxe_power_iteration",
     "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
     "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
-    "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather",
+    "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather", "maxe_entropy_levels",
 ]
 MAXE_BATCH_SCATTER_Y = 0x1
 
@@ -125,6 +126,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_batch_tune": [P, I32, P],
             "maxe_batch_plan_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32)],
             "maxe_vec_norm_gather": [P, I32, I32, P, P, P, P],
+            "maxe_entropy_levels": [P, I32, I32, I32, ctypes.c_double, P, P],
             "maxe_vec_dot_gather": [P, I32, I32, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -278,7 +280,8 @@ def maxe_permute_scatter(perm: torch.Tensor, y: torch.Tensor, stream=None):
 
 def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
-                     stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False) -> Handle:
+                     stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False,
+                     equal_rows: bool = False) -> Handle:
     """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity."""
     code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[val.dtype]
     _dev(rowptr, torch.int32, "rowptr")
@@ -292,7 +295,7 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
              val.data_ptr() if val.numel() else None, code)
     out = ctypes.c_void_p()
     flags = ((MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
-             | (MAXE_SPMM_LANES if spmm_lanes else 0))
+             | (MAXE_SPMM_LANES if spmm_lanes else 0) | (MAXE_EQUAL_ROWS if equal_rows else 0))
     _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
@@ -356,10 +359,10 @@ def maxe_version() -> str:
 
 
 def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False,
-             spmm_lanes=False) -> Handle:
+             spmm_lanes=False, equal_rows=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
     return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16,
-                            spmm_lanes)
+                            spmm_lanes, equal_rows)
 
 
 class Batch:
@@ -431,3 +434,13 @@ def maxe_vec_dot_gather(Q: torch.Tensor | None, u: torch.Tensor, w: torch.Tensor
     """out[0] = sum_j u[j] * w[Q[j]] (FP64)."""
     _check(load().maxe_vec_dot_gather(_ptr(Q), u.numel(), u.element_size(), _ptr(u), _ptr(w), _ptr(scratch),
                                       _ptr(out), ctypes.c_void_p(_stream(stream))), "maxe_vec_dot_gather")
+
+
+def maxe_entropy_levels(counts: torch.Tensor, L: int, base: float = 2.0, stream=None) -> torch.Tensor:
+    """(L, L) block entropies of a (gr, gc) int64 count grid (Section 5, hierarchical 2-D entropy)."""
+    _dev(counts, torch.int64, "counts")
+    gr, gc = counts.shape
+    out = torch.empty(L * L, dtype=torch.float64, device="cuda")
+    _check(load().maxe_entropy_levels(_ptr(counts), gr, gc, L, float(base), _ptr(out),
+                                      ctypes.c_void_p(_stream(stream))), "maxe_entropy_levels")
+    return out.view(L, L)

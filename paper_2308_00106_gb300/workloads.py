@@ -245,3 +245,15 @@ def serving_set(seed: int = 2308, count: int = 64, rows_lo: int = 10_000, rows_h
     lams = rng.uniform(lam_lo, lam_hi, count)
     return [poisson_uniform(seed * 7919 + m, int(rows[m]), float(lams[m]), "f32" if m % 2 == 0 else "bf16", device)
             for m in range(count)]
+
+
+def clustered_heavy(seed: int = 2308, n: int = 1 << 20, heavy_frac: float = 0.01, heavy_len: int = 1000,
+                    light_len: int = 16, dtype: str = "f32", device="cpu") -> CSR:
+    """Rows of two lengths, the heavy ones contiguous at the top: the shape Section 5
+    reports for LP OSA 07 (a handful of long rows next to one another), under which a
+    fixed equal-rows split is unbalanced until the rows are permuted. Distinct
+    uniform columns, U[-1, 1] values."""
+    nh = int(round(n * heavy_frac))
+    lengths = torch.full((n,), light_len, dtype=torch.int64, device=device)
+    lengths[:nh] = heavy_len
+    return from_lengths(seed, lengths, n, dtype, device)

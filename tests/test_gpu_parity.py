@@ -302,3 +302,84 @@ def test_invalid_arguments_are_rejected():
     assert lib.maxe_build_permutation(1, -1, 0, None, None, None) == maxe.MAXE_ERR_INVALID
     assert lib.maxe_build_permutation(1, 5, 2, None, None, None) == maxe.MAXE_ERR_INVALID
     assert lib.maxe_handle_destroy(None) == maxe.MAXE_OK
+
+
+# ------------------------------------------- equal-rows partition (Section 5)
+
+@pytest.mark.parametrize("kind", EDGE_KINDS + ["clustered"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_equal_rows_partition_products(kind, dtype):
+    """The fixed equal-rows split gives the oracle's products (SpMV, both SpMM
+    paths) in the original and the permuted space."""
+    A = (W.clustered_heavy(5, n=20000, heavy_len=900, dtype=dtype) if kind == "clustered"
+         else edge_matrix(kind, dtype, seed=8))
+    rperm, cperm = _perms(A, 13, "rc")
+    rp, co, va = A.numpy()
+    vd = "f64" if dtype == "f64" else "f32"
+    x = W.vector(3, A.cols, vd, "cuda")
+    X = W.matrix_rhs(3, A.cols, 6, vd, "cuda")
+    yo = oracle.spmv(A.rows, rp, co, va, code(dtype), x.cpu().numpy())
+    Yo = oracle.spmm(A.rows, rp, co, va, code(dtype), X.cpu().numpy())
+    for items16 in (False, True):
+        for lanes in (False, True):
+            h = maxe.from_csr(A.to("cuda"), rperm, cperm, equal_rows=True, items16=items16, spmm_lanes=lanes)
+            assert rel_l2(maxe.maxe_spmv(h, x).cpu().numpy(), yo) <= TOL[dtype]
+            assert rel_l2(maxe.maxe_spmm(h, X).cpu().numpy(), Yo) <= TOL[dtype]
+    nrp, nco, nva = oracle_permuted(A, rperm, cperm)
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, equal_rows=True)
+    xp = x[cperm.long()]
+    ypo = oracle.spmv(A.rows, nrp, nco, nva, code(dtype), xp.cpu().numpy())
+    assert rel_l2(maxe.maxe_spmv(h, xp, permuted=True).cpu().numpy(), ypo) <= TOL[dtype]
+
+
+def test_equal_rows_partition_unpermuted_and_deterministic():
+    A = W.clustered_heavy(9, n=50000, heavy_len=2000, dtype="f32").to("cuda")
+    x = W.vector(4, A.cols, "f32", "cuda")
+    h = maxe.from_csr(A, equal_rows=True)
+    rp, co, va = A.numpy()
+    yo = oracle.spmv(A.rows, rp, co, va, code("f32"), x.cpu().numpy())
+    y1 = maxe.maxe_spmv(h, x)
+    assert rel_l2(y1.cpu().numpy(), yo) <= TOL["f32"]
+    assert torch.equal(maxe.maxe_spmv(h, x), y1)
+
+
+# ------------------------------------- hierarchical 2-D entropy (Section 5)
+
+@pytest.mark.parametrize("grid,L", [((64, 64), 1), ((64, 64), 2), ((64, 64), 4), ((64, 64), 8), ((37, 53), 5),
+                                    ((512, 512), 64), ((3000, 7), 7), ((1, 1), 1)])
+def test_entropy_levels_against_oracle(grid, L):
+    A = edge_matrix("ragged", "f32", seed=6)
+    gr, gc = min(grid[0], A.rows), min(grid[1], A.cols)
+    for mode in ("plain", "rc"):
+        h = maxe.from_csr(A.to("cuda"), *_perms(A, 5, mode))
+        H, cnt = maxe.maxe_nnz_entropy(h, gr, gc)
+        for base in (2.0, math.e):
+            lv = maxe.maxe_entropy_levels(cnt, L, base).cpu().numpy()
+            ref = oracle.entropy_levels(cnt.cpu().numpy(), L, base)
+            np.testing.assert_allclose(lv, ref, rtol=1e-12, atol=1e-15)
+        if L == 1:
+            assert lv[0, 0] == pytest.approx(math.log(2) * H, rel=1e-12, abs=1e-15)
+
+
+def test_entropy_levels_permutation_flattens_the_map():
+    """Section 5: on a block-diagonal matrix the per-block entropies are uneven
+    (diagonal blocks far below log2 of their cell count); after row+column
+    permutation every block is within sampling noise of it (about 1,450 entries
+    over 256 cells here: an expected deficit near 0.13 bit)."""
+    A = W.blockdiag(2308, dtype="f64").to("cuda")
+    L, g = 4, 64
+    _, c0 = maxe.maxe_nnz_entropy(maxe.from_csr(A), g, g)
+    _, c1 = maxe.maxe_nnz_entropy(maxe.from_csr(A, *_perms(A, 3, "rc")), g, g)
+    m0 = maxe.maxe_entropy_levels(c0, L).cpu().numpy()
+    m1 = maxe.maxe_entropy_levels(c1, L).cpu().numpy()
+    full = math.log2((g // L) ** 2)
+    assert m1.min() > full - 0.25 and m1.max() <= full + 1e-12
+    assert m1.max() - m1.min() < 0.15 and m0.max() - m0.min() > 0.3
+    assert m0.min() < m1.min() - 1.0
+
+
+def test_entropy_levels_rejects_bad_split():
+    cnt = torch.ones(4, 4, dtype=torch.int64, device="cuda")
+    for L in (0, 5):
+        with pytest.raises(RuntimeError):
+            maxe.maxe_entropy_levels(cnt, L)
