@@ -561,6 +561,74 @@ def run_partition_table(args):
         print(json.dumps(out))
 
 
+def run_shuffle_table(args):
+    """The four randomisation formats of the appendix (R, RC, G-R, G-C) beside the
+    natural order: 64x64-grid entropy (Section 4), the spread of the 8x8
+    hierarchical entropy map (Section 5), one-time preprocessing time, and FP32
+    SpMV under the nnz-balanced and the equal-rows warp partitions."""
+    import oracle
+    from paper_2308_00106_gb300 import maxe
+    from paper_2308_00106_gb300 import workloads as W
+
+    rank, world, local = dist_setup(args)
+    maxe.load(build_if_missing=(rank == 0))
+    hbm, src = peaks()
+    K = max(10, args.steps // 100)
+    clocks = Clocks(local)
+    clocks.start()
+    rows_out = []
+    mats = (("blockdiag_4096", lambda: W.blockdiag(args.seed, dtype="f32", device="cuda")),
+            ("clustered_heavy_1M", lambda: W.clustered_heavy(args.seed, 1 << 20, dtype="f32", device="cuda")),
+            ("powerlaw_1M", lambda: W.powerlaw(args.seed, device="cuda")))
+    for wname, make in mats:
+        A = make()
+        M, N = A.rows, A.cols
+        x = W.vector(1, N, "f32", "cuda")
+        sample = np.random.default_rng(1).choice(M, size=min(M, 2000), replace=False)
+        for fmt in ("natural", "R", "RC", "G-R", "G-C"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if fmt in ("R", "RC"):
+                rperm = maxe.maxe_build_permutation(args.seed, M, 0)
+                cperm = maxe.maxe_build_permutation(args.seed, N, 1) if fmt == "RC" else None
+            elif fmt in ("G-R", "G-C"):
+                rperm, cperm = maxe.gradient_perms(A, args.seed, columns=(fmt == "G-C"))
+            else:
+                rperm = cperm = None
+            handles = {"nnz_balanced": maxe.from_csr(A, rperm, cperm)}
+            torch.cuda.synchronize()
+            t_pre = time.perf_counter() - t0
+            handles["equal_rows"] = maxe.from_csr(A, rperm, cperm, equal_rows=True)
+            h = handles["nnz_balanced"]
+            H, cnt = maxe.maxe_nnz_entropy(h, 64, 64)
+            lv = maxe.maxe_entropy_levels(cnt, 8).cpu().numpy()
+            xp = x[cperm.long()] if cperm is not None else x
+            row = {"matrix": wname, "format": fmt, "entropy_64x64": round(H, 4),
+                   "map8_min": round(float(lv.min()), 4), "map8_max": round(float(lv.max()), 4),
+                   "preprocess_ms": round(t_pre * 1e3, 3)}
+            rp, co, va, _, _ = h.csr()
+            ref = oracle.spmv_rows(rp.cpu().numpy(), co.cpu().numpy(), va.cpu().numpy(), W.DTYPE_CODE["f32"],
+                                   xp.cpu().double().numpy(), sample)
+            for part, hh in handles.items():
+                y = torch.empty(M, device="cuda")
+                step = lambda: maxe.maxe_spmv(hh, xp, y, permuted=True)  # noqa: E731
+                ms = timed_steps(step, K, 3, world, graph_len=10)
+                gbs = alg_bytes(M, N, A.nnz, 4, 4, 4) / (ms * 1e-3) / 1e9
+                got = y.cpu().double().numpy()[sample]
+                row[part] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                             "rel_l2_sampled": float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))}
+                hh.close()
+            rows_out.append(row)
+        del A
+    clk = clocks.stop()
+    out = {"metric": "entropy and FP32 SpMV GB/s per randomisation format (natural, R, RC, G-R, G-C)",
+           "unit": "GB/s", "peak": hbm, "peak_source": src,
+           "timing": f"{K} steps, CUDA graph of 10, CUDA events; preprocess = permutations + permute_csr, host clock",
+           "table": rows_out, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -568,7 +636,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["maxe", "reference"], default="maxe")
     ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag", "batched", "serving",
-                                           "laplacian-table", "partition-table"], default="powerlaw")
+                                           "laplacian-table", "partition-table", "shuffle-table"],
+                    default="powerlaw")
     ap.add_argument("--requests", type=int, default=1500, help="requests per serving trace")
     ap.add_argument("--batch-count", type=int, default=256, help="matrices of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: default batch plans, no autotuning")
@@ -588,6 +657,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "shuffle-table":
+        return run_shuffle_table(args)
     if args.workload == "partition-table":
         return run_partition_table(args)
     if args.workload == "laplacian-table":

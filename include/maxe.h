@@ -123,6 +123,34 @@ MAXE_API maxe_status maxe_build_permutation(uint64_t seed, int32_t n, int32_t ta
  * perm must be a bijection (not checked here; see MAXE_VALIDATE). */
 MAXE_API maxe_status maxe_invert_permutation(const int32_t* perm, int32_t n, int32_t* inv, void* stream);
 
+/* f1.  Nonzero histogram along one axis (Section 5 and the appendix's
+ * gradient-based permutations): axis 0 writes hist[i] = entries of row i
+ * (rows values), axis 1 writes hist[j] = entries of column j (cols values).
+ * A: (device arrays) the CSR; only rowptr (axis 0) or col (axis 1) is read.
+ * hist: (device) int32, written.  Exact (integer counts); stream-ordered.
+ * Errors: INVALID on a NULL pointer that is needed, axis not in {0,1}. */
+MAXE_API maxe_status maxe_nnz_histogram(const maxe_csr* A, int32_t axis, int32_t* hist, void* stream);
+
+/* f1.  Gradient-based permutation of n rows or columns (the appendix's
+ * "gradient based row permutation"; Section 5, Figures 4-5):
+ *   1. g_i = hist[i+1] - hist[i] for i = 0..n-2;
+ *   2. the cut is after the first i of maximum |g_i|: part one is [0, pivot),
+ *      part two [pivot, n), pivot = i + 1 (pivot = n when n < 2);
+ *   3. the parts are riffled, one card from each in turn starting with part
+ *      one, the longer part's remainder following in order;
+ *   4. each half of the shuffled deck (its first ceil(n/2) positions, and the
+ *      rest) is put in random order: the positions q of a half are sorted by
+ *      (key(seed, tag, q), q), the key of maxe_build_permutation.
+ * perm[new] = old, as for maxe_build_permutation; apply it with
+ * maxe_permute_csr (rows: tag 0 and the row histogram; columns: tag 1 and the
+ * column histogram).  hist: (device) int32[n] >= 0; perm: (device) int32[n],
+ * written; pivot: (device) int32[1] or NULL, receives the cut.  Deterministic.
+ * Errors: INVALID if n < 0, tag not in {0,1} or a needed pointer is NULL;
+ * OOM from the allocator. */
+MAXE_API maxe_status maxe_gradient_permutation(const int32_t* hist, int32_t n, uint64_t seed, int32_t tag,
+                                               int32_t* perm, int32_t* pivot, const maxe_allocator* alloc,
+                                               void* stream);
+
 /* a5.  Vector permutation of Eq. 1.  gather: out[i] = in[perm[i]] (x' = P_c^{-1} x);
  * scatter: out[perm[i]] = in[i] (y = P_r^{-1} y').  elem_bytes in {2, 4, 8};
  * in, out: (device) arrays of n elements, must not overlap. */

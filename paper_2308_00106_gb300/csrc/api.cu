@@ -101,6 +101,22 @@ maxe_status maxe_build_permutation(uint64_t seed, int32_t n, int32_t tag, int32_
   return radix_sort_pairs(keys, perm, keys_alt, vals_alt, n, 64, rs, st);
 }
 
+maxe_status maxe_nnz_histogram(const maxe_csr* A, int32_t axis, int32_t* hist, void* stream) {
+  if (!A || (axis != 0 && axis != 1)) return MAXE_ERR_INVALID;
+  if (bad_size(A->rows) || bad_size(A->cols) || bad_size(A->nnz) || !A->rowptr) return MAXE_ERR_INVALID;
+  if ((axis == 0 ? A->rows : A->cols) > 0 && !hist) return MAXE_ERR_INVALID;
+  if (axis == 1 && A->nnz > 0 && !A->col) return MAXE_ERR_INVALID;
+  return nnz_histogram_run(A->rowptr, A->col, A->rows, A->cols, A->nnz, axis, hist, as_stream(stream));
+}
+
+maxe_status maxe_gradient_permutation(const int32_t* hist, int32_t n, uint64_t seed, int32_t tag, int32_t* perm,
+                                      int32_t* pivot, const maxe_allocator* alloc, void* stream) {
+  if (n < 0 || (tag != 0 && tag != 1) || (n > 0 && (!hist || !perm))) return MAXE_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  Allocator al(alloc, st);
+  return gradient_permutation_run(hist, n, seed, tag, perm, pivot, al, st);
+}
+
 maxe_status maxe_invert_permutation(const int32_t* perm, int32_t n, int32_t* inv, void* stream) {
   if (n < 0 || (n > 0 && (!perm || !inv))) return MAXE_ERR_INVALID;
   return launch_invert(perm, n, inv, as_stream(stream));

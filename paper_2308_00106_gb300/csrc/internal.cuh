@@ -203,6 +203,12 @@ maxe_status scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, int32
                                int32_t* scratch, cudaStream_t st);
 // *p = v on the stream.
 maxe_status set_i32(int32_t* p, int32_t v, cudaStream_t st);
+// gradient.cu: entries per row (axis 0) or per column (axis 1); the gradient-based
+// permutation of n rows or columns from such a histogram.
+maxe_status nnz_histogram_run(const int32_t* rowptr, const int32_t* col, int32_t M, int32_t N, int64_t Z, int axis,
+                              int32_t* hist, cudaStream_t st);
+maxe_status gradient_permutation_run(const int32_t* hist, int32_t n, uint64_t seed, int32_t tag, int32_t* perm,
+                                     int32_t* pivot_out, const Allocator& al, cudaStream_t st);
 // first[g] = min{ i in [0, npos) : pos[i] >= g*H + off } (npos if none), g in [0, nb].
 maxe_status bucket_lower_bounds(const int32_t* pos, int64_t npos, int64_t H, int64_t off, int64_t nb,
                                 int32_t* first, cudaStream_t st);

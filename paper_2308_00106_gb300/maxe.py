@@ -38,6 +38,7 @@ EXPORTS = [
     "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
     "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
     "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather", "maxe_entropy_levels",
+    "maxe_nnz_histogram", "maxe_gradient_permutation",
 ]
 MAXE_BATCH_SCATTER_Y = 0x1
 
@@ -127,6 +128,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_batch_plan_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32)],
             "maxe_vec_norm_gather": [P, I32, I32, P, P, P, P],
             "maxe_entropy_levels": [P, I32, I32, I32, ctypes.c_double, P, P],
+            "maxe_nnz_histogram": [P, I32, P, P],
+            "maxe_gradient_permutation": [P, I32, ctypes.c_uint64, I32, P, P, P, P],
             "maxe_vec_dot_gather": [P, I32, I32, P, P, P, P, P],
         }
         for name, args in sig.items():
@@ -444,3 +447,42 @@ def maxe_entropy_levels(counts: torch.Tensor, L: int, base: float = 2.0, stream=
     _check(load().maxe_entropy_levels(_ptr(counts), gr, gc, L, float(base), _ptr(out),
                                       ctypes.c_void_p(_stream(stream))), "maxe_entropy_levels")
     return out.view(L, L)
+
+
+def _csr_struct(A) -> _Csr:
+    code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[A.val.dtype]
+    return _Csr(A.rows, A.cols, A.col.numel(), A.rowptr.data_ptr(),
+                   A.col.data_ptr() if A.col.numel() else None, A.val.data_ptr() if A.val.numel() else None, code)
+
+
+def maxe_nnz_histogram(A, axis: int, stream=None) -> torch.Tensor:
+    """Entries per row (axis 0) or per column (axis 1) of a CSR on the GPU (Section 5, appendix)."""
+    _dev(A.rowptr, torch.int32, "rowptr")
+    hist = torch.empty(A.rows if axis == 0 else A.cols, dtype=torch.int32, device="cuda")
+    s = _csr_struct(A)
+    _check(load().maxe_nnz_histogram(ctypes.byref(s), int(axis), _ptr(hist), ctypes.c_void_p(_stream(stream))),
+           "maxe_nnz_histogram")
+    return hist
+
+
+def maxe_gradient_permutation(hist: torch.Tensor, seed: int, tag: int, stream=None):
+    """(perm, pivot): cut at the steepest histogram step, riffle, random order in each
+    half of the shuffled deck (appendix, gradient-based permutations). pivot is a
+    one-element device tensor."""
+    _dev(hist, torch.int32, "hist")
+    n = hist.numel()
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    pivot = torch.empty(1, dtype=torch.int32, device="cuda")
+    _check(load().maxe_gradient_permutation(_ptr(hist), n, ctypes.c_uint64(seed & (2**64 - 1)), tag, _ptr(perm),
+                                            _ptr(pivot), ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream))),
+           "maxe_gradient_permutation")
+    return perm, pivot
+
+
+def gradient_perms(A, seed: int, columns: bool = False, stream=None):
+    """(rperm, cperm) of the gradient-based row (G-R) or row+column (G-C) permutation."""
+    rperm, _ = maxe_gradient_permutation(maxe_nnz_histogram(A, 0, stream), seed, 0, stream)
+    cperm = None
+    if columns:
+        cperm, _ = maxe_gradient_permutation(maxe_nnz_histogram(A, 1, stream), seed, 1, stream)
+    return rperm, cperm
