@@ -13,6 +13,7 @@ Each wrapper names the passage of the paper it states:
   entropy_levels                                               -- Section 5, hierarchical 2-D entropy
   nnz_histogram / gradient_permutation                         -- Section 5 and appendix, gradient shuffles
   spmv / spmm / spmv_rows                                      -- Section 2, CSR product
+  coo_spmv / csr_to_coo_rows                                   -- Section 2, COO product
   power_iteration                                              -- not in the paper (serving reference)
 
 Parity of the paper's printed entropies (8.39, 8.41, 11.27, ...) is unpinned:
@@ -68,6 +69,8 @@ def _load():
             lib.orc_nnz_entropy.argtypes = [_I32, _I32, _P, _P, _I32, _I32, ctypes.c_double, _P]
             lib.orc_spmv.argtypes = [_I32, _P, _P, _P, ctypes.c_int, _P, _P]
             lib.orc_entropy_levels.argtypes = [_P, _I32, _I32, _I32, ctypes.c_double, _P]
+            lib.orc_coo_spmv.argtypes = [_I32, _I64, _P, _P, _P, ctypes.c_int, _P, _P]
+            lib.orc_csr_to_coo_rows.argtypes = [_I32, _P, _P]
             lib.orc_nnz_histogram.argtypes = [_I32, _I32, _P, _P, _I32, _P]
             lib.orc_gradient_permutation.argtypes = [_P, _I32, ctypes.c_uint64, _I32, _P, _P]
             lib.orc_spmm.argtypes = [_I32, _P, _P, _P, ctypes.c_int, _I32, _P, _I64, _P, _I64]
@@ -199,6 +202,22 @@ def spmv(M: int, rowptr, col, val, dtype: int, x) -> np.ndarray:
     y = np.empty(M, dtype=np.float64)
     _load().orc_spmv(M, _ptr(rowptr), _ptr(col), _ptr(val), dtype, _ptr(x), _ptr(y))
     return y
+
+
+def coo_spmv(M: int, row, col, val, dtype: int, x) -> np.ndarray:
+    """y = A x over COO triplets in stored order, any order allowed (Section 2)."""
+    row, col, val, x = _i32(row), _i32(col), _vals(val, dtype), _f64(x)
+    y = np.empty(M, dtype=np.float64)
+    _load().orc_coo_spmv(M, row.size, _ptr(row), _ptr(col), _ptr(val), dtype, _ptr(x), _ptr(y))
+    return y
+
+
+def csr_to_coo_rows(M: int, rowptr) -> np.ndarray:
+    """Row index of every stored entry of a CSR matrix (its COO form, Section 2)."""
+    rowptr = _i32(rowptr)
+    row = np.empty(int(rowptr[M]) if M > 0 else 0, dtype=np.int32)
+    _load().orc_csr_to_coo_rows(M, _ptr(rowptr), _ptr(row))
+    return row
 
 
 def spmm(M: int, rowptr, col, val, dtype: int, X) -> np.ndarray:

@@ -326,6 +326,20 @@ void orc_spmv(int32_t M, const int32_t* rowptr, const int32_t* col, const void* 
   }
 }
 
+/* COO product (Section 2: triplets (ROW, COL, VALUE), no order required):
+ * y = 0, then y[row[t]] += value[t] * x[col[t]] for t = 0..Z-1 in stored order. */
+void orc_coo_spmv(int32_t M, int64_t Z, const int32_t* row, const int32_t* col, const void* val, int dtype,
+                  const double* x, double* y) {
+  for (int32_t i = 0; i < M; ++i) y[i] = 0.0;
+  for (int64_t t = 0; t < Z; ++t) y[row[t]] += orc_decode(val, dtype, t) * x[col[t]];
+}
+
+/* Row indices of the COO form of a CSR matrix: row[t] = i for rowptr[i] <= t < rowptr[i+1]. */
+void orc_csr_to_coo_rows(int32_t M, const int32_t* rowptr, int32_t* row) {
+  for (int32_t i = 0; i < M; ++i)
+    for (int32_t t = rowptr[i]; t < rowptr[i + 1]; ++t) row[t] = i;
+}
+
 /* Same product for k right-hand sides: X row-major N x k (leading dim ldx),
  * Y row-major M x k (leading dim ldy). */
 void orc_spmm(int32_t M, const int32_t* rowptr, const int32_t* col, const void* val,

@@ -167,6 +167,23 @@ def test_spmm_matches_dense_brute_force():
     np.testing.assert_allclose(oracle.spmv_rows(rp, co, va, 1, X[:, 2], rows), (D @ X[:, 2])[rows], rtol=1e-13)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_coo_spmv_matches_dense_and_any_triplet_order(dtype):
+    A = small_csr(51, 45, 38, dtype, density=0.3)
+    rp, co, va = A.numpy()
+    row = oracle.csr_to_coo_rows(45, rp)
+    np.testing.assert_array_equal(row, np.repeat(np.arange(45), np.diff(rp)))
+    x = np.random.default_rng(3).uniform(-1, 1, 38)
+    D = dense_of(45, 38, rp, co, decode(va, W.DTYPE_CODE[dtype]))
+    y = oracle.coo_spmv(45, row, co, va, W.DTYPE_CODE[dtype], x)
+    np.testing.assert_allclose(y, D @ x, rtol=1e-13, atol=1e-14)
+    perm = np.random.default_rng(4).permutation(row.size)  # COO keeps no order
+    y2 = oracle.coo_spmv(45, row[perm], co[perm], va[perm], W.DTYPE_CODE[dtype], x)
+    np.testing.assert_allclose(y2, y, rtol=1e-13, atol=1e-14)
+    # in CSR order the sums run in the same order as the CSR product: identical
+    np.testing.assert_array_equal(y, oracle.spmv(45, rp, co, va, W.DTYPE_CODE[dtype], x))
+
+
 def test_spmv_empty_matrix_and_empty_rows():
     rowptr = np.zeros(4, dtype=np.int32)
     y = oracle.spmv(3, rowptr, np.zeros(0, np.int32), np.zeros(0), 0, np.ones(5))
