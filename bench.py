@@ -513,9 +513,11 @@ def run_laplacian_table(args):
 
 def run_partition_table(args):
     """Equal-rows versus nnz-balanced warp partitions (Section 5: a fixed split by
-    equal rows is where random permutation balances the load), natural and
-    permuted order, FP32 SpMV, on two 1M-row matrices: heavy rows clustered at
-    the top (1% of rows x 1000 entries, the rest 16) and the power-law matrix."""
+    equal rows is where random permutation balances the load) and the COO
+    product (Section 2), natural and permuted order, FP32 SpMV, on two 1M-row
+    matrices: heavy rows clustered at the top (1% of rows x 1000 entries, the
+    rest 16) and the power-law matrix.  GB/s counts the CSR's algorithmic bytes
+    for all three, so they compare as times."""
     import oracle
     from paper_2308_00106_gb300 import maxe
     from paper_2308_00106_gb300 import workloads as W
@@ -535,14 +537,17 @@ def run_partition_table(args):
         x = W.vector(1, N, "f32", "cuda")
         sample = np.random.default_rng(1).choice(M, size=2000, replace=False)
         for order in ("natural", "permuted"):
-            for part in ("nnz_balanced", "equal_rows"):
+            for part in ("nnz_balanced", "equal_rows", "coo"):
                 perms = (rperm, cperm) if order == "permuted" else (None, None)
-                h = maxe.from_csr(A, *perms, equal_rows=(part == "equal_rows"))
+                h = maxe.from_csr(A, *perms, equal_rows=(part == "equal_rows"), coo=(part == "coo"))
                 xp = x[cperm.long()] if order == "permuted" else x
                 y = torch.empty(M, device="cuda")
-                step = lambda: maxe.maxe_spmv(h, xp, y, permuted=True)  # noqa: E731
+                if part == "coo":
+                    step = lambda: maxe.maxe_coo_spmv(h, xp, y, permuted=True)  # noqa: E731
+                else:
+                    step = lambda: maxe.maxe_spmv(h, xp, y, permuted=True)  # noqa: E731
                 ms = timed_steps(step, K, 3, world, graph_len=10)
-                gbs = alg_bytes(M, N, A.nnz, 4, 4, 4) / (ms * 1e-3) / 1e9
+                gbs = alg_bytes(M, N, A.nnz, 4, 4, 4) / (ms * 1e-3) / 1e9  # CSR bytes: COO reads 4 more per entry
                 rp, co, va, _, _ = h.csr()
                 ref = oracle.spmv_rows(rp.cpu().numpy(), co.cpu().numpy(), va.cpu().numpy(), W.DTYPE_CODE["f32"],
                                        xp.cpu().double().numpy(), sample)
@@ -553,7 +558,7 @@ def run_partition_table(args):
                 h.close()
         del A
     clk = clocks.stop()
-    out = {"metric": "FP32 SpMV GB/s, equal-rows vs nnz-balanced warp partition, natural vs permuted",
+    out = {"metric": "FP32 SpMV GB/s, equal-rows vs nnz-balanced warp partition vs COO, natural vs permuted",
            "unit": "GB/s", "peak": hbm, "peak_source": src,
            "timing": f"{K} steps, CUDA graph of 10, CUDA events; inputs larger than L2",
            "table": rows_out, "clocks": clk}

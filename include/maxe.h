@@ -81,6 +81,11 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * partition under which the paper finds that random permutation balances the
  * load (Section 6, parallel CSR and GPU CSR by equal rows). */
 #define MAXE_EQUAL_ROWS 0x20u
+/* Flag of maxe_permute_csr: also keep the COO form of A' (Section 2: triplets
+ * ROW, COL, VALUE) -- a row index per entry beside the CSR's columns and
+ * values -- for maxe_coo_spmv.  Costs 4 bytes per entry plus 17 bytes (FP64:
+ * 17, else 9) per 256 entries. */
+#define MAXE_COO 0x40u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -165,7 +170,7 @@ MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_
  * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
  * (the "plain" matrix).  The handle keeps its own copies of the permutations.
  * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16, MAXE_SPMM_LANES,
- * MAXE_EQUAL_ROWS.  *out receives the new handle.
+ * MAXE_EQUAL_ROWS, MAXE_COO.  *out receives the new handle.
  * Synchronises `stream` once (to size the pass over rows longer than 2048).
  * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
 MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
@@ -233,6 +238,19 @@ MAXE_API maxe_status maxe_nnz_entropy_noalloc(const maxe_handle* h, int32_t gr, 
  * handles, FP32 otherwise.  x and y must not overlap.  Calls on one handle
  * without MAXE_VEC_PERMUTED share its x' scratch: do not overlap them in time. */
 MAXE_API maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uint32_t flags, void* stream);
+
+/* f3.  y = A x over the COO form of the handle (Section 2, COO product): the
+ * row-sorted triplets of A' in chunks of 256 entries, one warp per chunk,
+ * rows that cross chunk edges finished by a second kernel from per-chunk
+ * partial sums in chunk order (deterministic).  Vectors, flags and the x'
+ * scratch as for maxe_spmv.  Errors: UNSUPPORTED if the handle was created
+ * without MAXE_COO; INVALID on NULL pointers or unknown flags. */
+MAXE_API maxe_status maxe_coo_spmv(const maxe_handle* h, const void* x, void* y, uint32_t flags, void* stream);
+
+/* The handle's COO row indices: *row = (device) int32[nnz], row[t] = i for the
+ * entries t of row i of A' (library-owned, valid until the handle is destroyed).
+ * Errors: UNSUPPORTED without MAXE_COO. */
+MAXE_API maxe_status maxe_handle_coo(const maxe_handle* h, const int32_t** row);
 
 /* a7.  Y = A X for k right-hand sides (1 <= k <= 64).  X: (device) row-major
  * cols x k with leading dimension ldx >= k; Y: (device) row-major rows x k,

@@ -42,6 +42,8 @@ void release(maxe_handle* h) {
   if (!h) return;
   const Allocator& al = h->al;
   al.put(h->xbuf);
+  al.put(h->coo_carry);
+  al.put(h->coo_row);
   al.put(h->bwrow);
   al.put(h->wrow[1]);
   al.put(h->wrow[0]);
@@ -144,7 +146,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return MAXE_ERR_INVALID;
   if (A->nnz > 0 && (A->rows == 0 || A->cols == 0)) return MAXE_ERR_INVALID;
   if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16 | MAXE_SPMM_LANES |
-                                     MAXE_EQUAL_ROWS))
+                                     MAXE_EQUAL_ROWS | MAXE_COO))
     return MAXE_ERR_INVALID;
   DeviceInfo di{};
   MAXE_TRY(device_info(&di));
@@ -162,6 +164,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   h->equal_rows = (flags & MAXE_EQUAL_ROWS) ? 1 : 0;
   maxe_status s = permute_csr_run(A, rperm, cperm, flags, h, st);
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
+  if (s == MAXE_OK && (flags & MAXE_COO)) s = coo_build(h, st);
   if (s == MAXE_OK) s = batch_plan_default(h, st);
   if (s == MAXE_OK && (flags & MAXE_ITEMS16)) h->spmv_items16 = 1;
   if (s == MAXE_OK && (flags & MAXE_SPMM_LANES)) h->spmm_lc = 1;
@@ -215,6 +218,26 @@ maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uint32_t fla
     xs = h->xbuf;
   }
   return spmm_launch(h, 1, xs, 1, y, 1, h->rperm, st);
+}
+
+maxe_status maxe_coo_spmv(const maxe_handle* h, const void* x, void* y, uint32_t flags, void* stream) {
+  if (!h || flags & ~static_cast<uint32_t>(MAXE_VEC_PERMUTED)) return MAXE_ERR_INVALID;
+  if ((h->cols > 0 && !x) || (h->rows > 0 && !y)) return MAXE_ERR_INVALID;
+  if (!h->coo_row) return MAXE_ERR_UNSUPPORTED;
+  cudaStream_t st = as_stream(stream);
+  if (flags & MAXE_VEC_PERMUTED) return coo_spmv_launch(h, x, y, nullptr, st);
+  const void* xs = x;
+  if (h->cperm) {
+    MAXE_TRY(launch_gather(h->cperm, h->cols, vector_bytes(h->dtype), 1, x, 1, h->xbuf, 1, st));
+    xs = h->xbuf;
+  }
+  return coo_spmv_launch(h, xs, y, h->rperm, st);
+}
+
+maxe_status maxe_handle_coo(const maxe_handle* h, const int32_t** row) {
+  if (!h || !row) return MAXE_ERR_INVALID;
+  *row = h->coo_row;
+  return h->coo_row ? MAXE_OK : MAXE_ERR_UNSUPPORTED;
 }
 
 maxe_status maxe_spmm(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,

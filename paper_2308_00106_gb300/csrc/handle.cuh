@@ -7,6 +7,8 @@
 //   wrow    [nW + 1]                       SpMV work partition: first row of each warp range
 //   rperm, cperm [rows], [cols]            copies of the permutations (or NULL)
 //   xbuf                                   x' = P_c^{-1} x scratch for original-space calls
+//   coo_row [nnz], coo_carry               COO form (MAXE_COO): row of each entry, and
+//                                          per-256-entry-chunk partial sums + flags
 // nnz_pad leaves at least two 128-entry pieces of zeros after the last entry,
 // so the SpMV warps can load whole aligned pieces (and prefetch one ahead)
 // without a bounds test.
@@ -33,6 +35,8 @@ struct maxe_handle {
   int64_t bH = 0;
   int bit16 = 0;                           // batch plan: 16 entries per lane for k = 1
   int blc = 0;                             // batch plan: SpMM with columns across lanes
+  int32_t* coo_row = nullptr;              // COO row index of every entry (MAXE_COO), else NULL
+  void* coo_carry = nullptr;               // COO per-chunk partial sums and flags
   void* xbuf = nullptr;  // cols * k_cap vector elements
   int32_t xbuf_k = 0;
   maxe::Allocator al;
@@ -62,6 +66,11 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st);
 constexpr int64_t kDefaultBatchTask = 2048;  // entries per warp task of the default batch plan
 maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc);
 maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st);
+
+// coo.cu: the COO row indices and chunk carries of a handle; y = A' x over them
+// (rows optionally scattered through yperm).
+maxe_status coo_build(maxe_handle* h, cudaStream_t st);
+maxe_status coo_spmv_launch(const maxe_handle* h, const void* x, void* y, const int32_t* yperm, cudaStream_t st);
 
 // entropy.cu
 maxe_status entropy_run(const maxe_handle* h, int32_t gr, int32_t gc, double base, double* H_host,

@@ -27,6 +27,7 @@ MAXE_AUTOTUNE = 0x4
 MAXE_ITEMS16 = 0x8
 MAXE_SPMM_LANES = 0x10
 MAXE_EQUAL_ROWS = 0x20
+MAXE_COO = 0x40
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -38,7 +39,7 @@ EXPORTS = [
     "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
     "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
     "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather", "maxe_entropy_levels",
-    "maxe_nnz_histogram", "maxe_gradient_permutation",
+    "maxe_nnz_histogram", "maxe_gradient_permutation", "maxe_coo_spmv", "maxe_handle_coo",
 ]
 MAXE_BATCH_SCATTER_Y = 0x1
 
@@ -129,6 +130,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_vec_norm_gather": [P, I32, I32, P, P, P, P],
             "maxe_entropy_levels": [P, I32, I32, I32, ctypes.c_double, P, P],
             "maxe_nnz_histogram": [P, I32, P, P],
+            "maxe_coo_spmv": [P, P, P, ctypes.c_uint32, P],
+            "maxe_handle_coo": [P, ctypes.POINTER(ctypes.c_void_p)],
             "maxe_gradient_permutation": [P, I32, ctypes.c_uint64, I32, P, P, P, P],
             "maxe_vec_dot_gather": [P, I32, I32, P, P, P, P, P],
         }
@@ -217,6 +220,12 @@ class Handle:
                 _view(v.val, self.nnz, VAL_TORCH[self.dtype]), _view(rp.value, self.rows, torch.int32),
                 _view(cp.value, self.cols, torch.int32))
 
+    def coo_rows(self):
+        """COO row index of every entry (zero-copy view), for handles made with coo=True."""
+        r = ctypes.c_void_p()
+        _check(load().maxe_handle_coo(ctypes.c_void_p(self.ptr), ctypes.byref(r)), "maxe_handle_coo")
+        return _view(r.value, self.nnz, torch.int32)
+
     def items_per_lane(self) -> int:
         """Entries per lane of the SpMV kernel variant this handle uses (8 or 16)."""
         return self._tuning() & 0xFF
@@ -284,7 +293,7 @@ def maxe_permute_scatter(perm: torch.Tensor, y: torch.Tensor, stream=None):
 def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
                      stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False,
-                     equal_rows: bool = False) -> Handle:
+                     equal_rows: bool = False, coo: bool = False) -> Handle:
     """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity."""
     code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[val.dtype]
     _dev(rowptr, torch.int32, "rowptr")
@@ -298,7 +307,8 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
              val.data_ptr() if val.numel() else None, code)
     out = ctypes.c_void_p()
     flags = ((MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
-             | (MAXE_SPMM_LANES if spmm_lanes else 0) | (MAXE_EQUAL_ROWS if equal_rows else 0))
+             | (MAXE_SPMM_LANES if spmm_lanes else 0) | (MAXE_EQUAL_ROWS if equal_rows else 0)
+             | (MAXE_COO if coo else 0))
     _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
@@ -324,6 +334,19 @@ def maxe_spmv(h: Handle, x: torch.Tensor, y: torch.Tensor | None = None, permute
     _dev(y, h.vec_dtype, "y")
     _check(load().maxe_spmv(ctypes.c_void_p(h.ptr), _ptr(x), _ptr(y), MAXE_VEC_PERMUTED if permuted else 0,
                             ctypes.c_void_p(_stream(stream))), "maxe_spmv")
+    return y
+
+
+def maxe_coo_spmv(h: Handle, x: torch.Tensor, y: torch.Tensor | None = None, permuted: bool = False, stream=None):
+    """y = A x over the handle's COO triplets (Section 2); needs a handle made with coo=True."""
+    _dev(x, h.vec_dtype, "x")
+    if x.numel() != h.cols:
+        raise ValueError("x has the wrong length")
+    if y is None:
+        y = torch.empty(h.rows, dtype=h.vec_dtype, device="cuda")
+    _dev(y, h.vec_dtype, "y")
+    _check(load().maxe_coo_spmv(ctypes.c_void_p(h.ptr), _ptr(x), _ptr(y), MAXE_VEC_PERMUTED if permuted else 0,
+                                ctypes.c_void_p(_stream(stream))), "maxe_coo_spmv")
     return y
 
 
@@ -362,10 +385,10 @@ def maxe_version() -> str:
 
 
 def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False,
-             spmm_lanes=False, equal_rows=False) -> Handle:
+             spmm_lanes=False, equal_rows=False, coo=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
     return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16,
-                            spmm_lanes, equal_rows)
+                            spmm_lanes, equal_rows, coo)
 
 
 class Batch:
