@@ -777,7 +777,8 @@ def main():
         "plain": {"value": round(gbs_plain * world, 3), "unit": "GB/s", "ms_per_step": ms_plain,
                   "frac": round(gbs_plain / hbm, 4)},
         "permuted_over_plain": round(ms_plain / ms_perm, 4),
-        "kernel_variant": {"permuted_items_per_lane": hP.items_per_lane(), "plain_items_per_lane": hN.items_per_lane()},
+        "kernel_variant": {"permuted_items_per_lane": hP.items_per_lane(), "plain_items_per_lane": hN.items_per_lane(),
+                           "permuted_xslice": hP.xslice(), "plain_xslice": hN.xslice()},
         "flushed_l2_launch_ms": {"permuted": fl_perm, "plain": fl_plain},
         "full_path": {"value": round(bytes_step / (ms_full * 1e-3) / 1e9, 3), "unit": "GB/s",
                       "ms_per_step": ms_full, "what": "y = A x in the original space: x gather + SpMV with fused "

@@ -86,6 +86,17 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * values -- for maxe_coo_spmv.  Costs 4 bytes per entry plus 17 bytes (FP64:
  * 17, else 9) per 256 entries. */
 #define MAXE_COO 0x40u
+/* Flag of maxe_permute_csr: also build the x-sliced form of A' and use it for
+ * SpMV (k = 1, 16-byte aligned x).  The columns are cut into 64 KB slices of x
+ * (16384 FP32 / 8192 FP64 columns), the rows into one tile per SM; each tile's
+ * warps own row ranges and read their entries slice by slice, gathering x from
+ * shared memory instead of L2 (one L2 request per nonzero on a randomly
+ * permuted matrix is what bounds the CSR kernel there).  Costs 4 + value-size
+ * bytes per entry more memory and a synchronising build.  MAXE_AUTOTUNE builds
+ * it too when its x traffic would stay under four times the matrix, and keeps
+ * it only if it times faster than the CSR kernel.  Ignored with
+ * MAXE_EQUAL_ROWS.  Deterministic. */
+#define MAXE_XSLICE 0x80u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -170,7 +181,7 @@ MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_
  * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
  * (the "plain" matrix).  The handle keeps its own copies of the permutations.
  * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16, MAXE_SPMM_LANES,
- * MAXE_EQUAL_ROWS, MAXE_COO.  *out receives the new handle.
+ * MAXE_EQUAL_ROWS, MAXE_COO, MAXE_XSLICE.  *out receives the new handle.
  * Synchronises `stream` once (to size the pass over rows longer than 2048).
  * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
 MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
@@ -185,7 +196,8 @@ MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, c
 
 /* Kernel variants of the handle, as chosen by MAXE_AUTOTUNE / MAXE_ITEMS16 /
  * MAXE_SPMM_LANES at creation: *items = entries per lane of the SpMV variant
- * (8 or 16), plus 0x100 when SpMM uses columns across lanes.  items: (host). */
+ * (8 or 16), plus 0x100 when SpMM uses columns across lanes, plus 0x200 when
+ * SpMV uses the x-sliced form (MAXE_XSLICE).  items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;

@@ -42,6 +42,7 @@ void release(maxe_handle* h) {
   if (!h) return;
   const Allocator& al = h->al;
   al.put(h->xbuf);
+  xslice_release(h);
   al.put(h->coo_carry);
   al.put(h->coo_row);
   al.put(h->bwrow);
@@ -146,7 +147,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return MAXE_ERR_INVALID;
   if (A->nnz > 0 && (A->rows == 0 || A->cols == 0)) return MAXE_ERR_INVALID;
   if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16 | MAXE_SPMM_LANES |
-                                     MAXE_EQUAL_ROWS | MAXE_COO))
+                                     MAXE_EQUAL_ROWS | MAXE_COO | MAXE_XSLICE))
     return MAXE_ERR_INVALID;
   DeviceInfo di{};
   MAXE_TRY(device_info(&di));
@@ -165,6 +166,8 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   maxe_status s = permute_csr_run(A, rperm, cperm, flags, h, st);
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
   if (s == MAXE_OK && (flags & MAXE_COO)) s = coo_build(h, st);
+  if (s == MAXE_OK && (flags & (MAXE_XSLICE | MAXE_AUTOTUNE)) && !h->equal_rows)
+    s = xslice_build(h, st, (flags & MAXE_XSLICE) != 0);
   if (s == MAXE_OK) s = batch_plan_default(h, st);
   if (s == MAXE_OK && (flags & MAXE_ITEMS16)) h->spmv_items16 = 1;
   if (s == MAXE_OK && (flags & MAXE_SPMM_LANES)) h->spmm_lc = 1;
@@ -194,7 +197,7 @@ maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view, const int32_t*
 
 maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
   if (!h || !items) return MAXE_ERR_INVALID;
-  *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0);
+  *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0) | (h->xs_use ? 0x200 : 0);
   return MAXE_OK;
 }
 

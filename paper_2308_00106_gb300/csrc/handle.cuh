@@ -35,6 +35,18 @@ struct maxe_handle {
   int64_t bH = 0;
   int bit16 = 0;                           // batch plan: 16 entries per lane for k = 1
   int blc = 0;                             // batch plan: SpMM with columns across lanes
+  // x-sliced SpMV form (MAXE_XSLICE): entries grouped by (warp range, column slice)
+  uint32_t* xs_idx = nullptr;              // (tile-local row << slice bits) | column in slice
+  void* xs_val = nullptr;
+  int32_t* xs_seg_start = nullptr;         // [G * nS], xs_seg_len follows in the same block
+  int32_t* xs_seg_len = nullptr;
+  int32_t* xs_tile_row = nullptr;          // [ntiles + 1]
+  int32_t* xs_warp_row = nullptr;          // [G + 1]
+  int32_t* xs_tl_off = nullptr;            // [ntiles + 1], xs_tl_slice follows in the same block
+  int32_t* xs_tl_slice = nullptr;
+  int32_t xs_ntiles = 0, xs_nS = 0;
+  int64_t xs_bytes = 0;
+  int xs_use = 0;                          // SpMV (k = 1) takes the x-sliced kernel
   int32_t* coo_row = nullptr;              // COO row index of every entry (MAXE_COO), else NULL
   void* coo_carry = nullptr;               // COO per-chunk partial sums and flags
   void* xbuf = nullptr;  // cols * k_cap vector elements
@@ -66,6 +78,14 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st);
 constexpr int64_t kDefaultBatchTask = 2048;  // entries per warp task of the default batch plan
 maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc);
 maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st);
+
+// xslice.cu: build the x-sliced form (unless forced, leaves it unbuilt when it
+// would not pay);
+// launch y' = A' x' with it (x 16-byte aligned, unit strides); free it.
+maxe_status xslice_build(maxe_handle* h, cudaStream_t st, bool force);
+bool xslice_ready(const maxe_handle* h, const void* x);
+maxe_status xslice_launch(const maxe_handle* h, const void* x, void* y, const int32_t* yperm, cudaStream_t st);
+void xslice_release(maxe_handle* h);
 
 // coo.cu: the COO row indices and chunk carries of a handle; y = A' x over them
 // (rows optionally scattered through yperm).

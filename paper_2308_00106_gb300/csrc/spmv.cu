@@ -176,6 +176,7 @@ maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t 
       vw = 2;
   }
   const bool unit = k == 1 && ldx == 1 && ldy == 1;
+  if (unit && variant < 0 && lc < 0 && xslice_ready(h, X)) return xslice_launch(h, X, Y, yperm, st);
   const int it = (unit && variant < 0) ? h->spmv_items16 : (variant > 0 ? 1 : 0);
   if (it == 1 && !unit) return MAXE_ERR_UNSUPPORTED;
   p.wrow = h->wrow[it];
@@ -233,6 +234,12 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st) {
     }
   }
   h->spmv_items16 = pick;
+  // the x-sliced kernel, when the handle has it
+  if (s == MAXE_OK && h->xs_idx) {
+    float ms = 0.f;
+    s = timed([&] { return xslice_launch(h, x, y, nullptr, st); }, &ms);
+    if (s == MAXE_OK) h->xs_use = ms < best ? 1 : 0;
+  }
   // SpMM path for wide right-hand sides, timed at k = 16 when the scratch is modest
   const int64_t k = 16;
   const int64_t bytes = (static_cast<int64_t>(h->rows) + h->cols) * k * eb;

@@ -1,0 +1,663 @@
+// xslice.cu -- SpMV with x staged in shared memory by column slices.
+//
+// On a randomly permuted matrix every nonzero of the CSR kernel gathers x[col]
+// from a random address: one L2 request per nonzero, which bounds the product
+// well below HBM bandwidth.  Here the columns are cut into slices of S = 2^14
+// (FP32) / 2^13 (FP64) columns, 64 KB of x each, and the matrix into tiles of
+// consecutive rows, one tile per SM at a time:
+//
+//   - a producer warp loads the slices of x the tile touches, in order, into a
+//     shared-memory ring of three (FP64: two) slices with 1-D bulk copies (TMA;
+//     64 KB, L2 evict-last so x stays in L2 for the other SMs);
+//   - 16 consumer warps each own a contiguous range of the tile's rows
+//     (nnz-balanced) and a row accumulator per row in shared memory; for every
+//     slice a warp streams its own entries of that slice -- (row, column in
+//     slice) packed in 32 bits, and the value -- with 16-byte loads, gathers x
+//     from shared memory, sums rows with a segmented shuffle scan and adds each
+//     row's partial sum to its accumulator;
+//   - at the end of the tile every warp writes its rows of y (through rperm
+//     when y is wanted in the original space).
+//
+// Each accumulator is touched by one warp only, in slice order and then entry
+// order, so the result is deterministic.  The format is built once from the
+// handle's CSR (a stable sort by (warp range, slice)); it pays when the rows of
+// a tile hit most x sectors of the slices they touch, i.e. for matrices with
+// many nonzeros per column of a tile (the 1M-row power-law matrix permuted),
+// and unless asked for explicitly it is skipped when the estimated x traffic
+// exceeds four times the matrix.
+#include <algorithm>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace maxe {
+namespace {
+
+constexpr int kXsWarps = 15;  // consumer warps per CTA; with the producer, 4 warps per SM sub-partition
+constexpr int kXsThreads = 32 * (kXsWarps + 1);
+constexpr int kXsItems = 8;  // entries per lane per chunk
+constexpr int kXsChunk = 32 * kXsItems;
+constexpr int kXsAlign = 8;    // segment starts padded to 8 entries: 16-byte loads of idx and values
+constexpr int kXsSlack = 256;  // zeroed entries after the last segment (whole-vector loads at the end)
+
+template <typename VT>
+struct XsCfg;
+template <>
+struct XsCfg<float> {
+  static constexpr int kSliceBits = 14;  // 16384 columns, 64 KB
+  static constexpr int kBuffers = 3;     // slices in the ring: two loads in flight while one is read
+  static constexpr int kRows = 8192;     // rows per tile, 32 KB of accumulators
+  static constexpr int kDepth = 3;       // chunks per warp in registers (one summed, the rest in flight)
+};
+template <>
+struct XsCfg<double> {
+  static constexpr int kSliceBits = 13;  // 8192 columns, 64 KB
+  static constexpr int kBuffers = 2;
+  static constexpr int kRows = 8192;     // 64 KB
+  static constexpr int kDepth = 2;
+};
+
+template <typename VT>
+constexpr size_t xs_smem_bytes() {
+  return sizeof(VT) * (XsCfg<VT>::kBuffers * (size_t(1) << XsCfg<VT>::kSliceBits) + XsCfg<VT>::kRows) +
+         16 * XsCfg<VT>::kBuffers + 16;
+}
+
+struct XsParams {
+  const uint32_t* idx;        // (tile-local row << kSliceBits) | column in slice
+  const void* val;            // values, aligned with idx
+  const int32_t* seg_start;   // [G * nS] first entry of (warp range, slice)
+  const int32_t* seg_len;     // [G * nS] entries of (warp range, slice)
+  const int32_t* tile_row;    // [ntiles + 1]
+  const int32_t* warp_row;    // [G + 1] first (global) row of each warp range
+  const int32_t* tl_off;      // [ntiles + 1] into tl_slice
+  const int32_t* tl_slice;    // slices touched by each tile, ascending
+  int32_t ntiles, nS, N;
+  const void* x;
+  void* y;
+  const int32_t* yperm;
+  unsigned* status;
+};
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+template <typename VT>
+struct XsVals;
+template <>
+struct XsVals<double> {  // FP64 values
+  using AT = double;
+  static __device__ __forceinline__ void load(const void* v, int64_t e, double (&a)[kXsItems]) {
+    const double2* p = reinterpret_cast<const double2*>(static_cast<const double*>(v) + e);
+#pragma unroll
+    for (int q = 0; q < kXsItems / 2; ++q) {
+      const double2 t = __ldcs(p + q);
+      a[2 * q] = t.x;
+      a[2 * q + 1] = t.y;
+    }
+  }
+};
+template <>
+struct XsVals<float> {  // FP32 values
+  using AT = float;
+  static __device__ __forceinline__ void load(const void* v, int64_t e, float (&a)[kXsItems]) {
+    const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(v) + e);
+#pragma unroll
+    for (int q = 0; q < kXsItems / 4; ++q) {
+      const float4 t = __ldcs(p + q);
+      a[4 * q] = t.x;
+      a[4 * q + 1] = t.y;
+      a[4 * q + 2] = t.z;
+      a[4 * q + 3] = t.w;
+    }
+  }
+};
+template <>
+struct XsVals<uint16_t> {  // BF16 values, FP32 arithmetic
+  using AT = float;
+  static __device__ __forceinline__ void load(const void* v, int64_t e, float (&a)[kXsItems]) {
+    const uint4 t = __ldcs(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(v) + e));
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[2 * q] = __uint_as_float(w[q] << 16);
+      a[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+    }
+  }
+};
+
+// One chunk of a warp's entries in registers: 8 consecutive entries per lane.
+template <typename VT>
+struct XsChunk {
+  uint32_t id[kXsItems];
+  VT a[kXsItems];
+  int nval;  // valid entries of this lane (<= 0: none)
+};
+
+template <typename VT, typename ValT>
+__device__ __forceinline__ void xs_load(const XsParams& p, int32_t st, int32_t len, int32_t c, int lane,
+                                        XsChunk<VT>& k) {
+  const int32_t off = c + lane * kXsItems;
+  k.nval = min(kXsItems, len - off);
+  if (k.nval > 0) {
+    const uint4* ip = reinterpret_cast<const uint4*>(p.idx + st + off);
+    const uint4 u0 = __ldcs(ip), u1 = __ldcs(ip + 1);
+    k.id[0] = u0.x, k.id[1] = u0.y, k.id[2] = u0.z, k.id[3] = u0.w;
+    k.id[4] = u1.x, k.id[5] = u1.y, k.id[6] = u1.z, k.id[7] = u1.w;
+    XsVals<ValT>::load(p.val, static_cast<int64_t>(st) + off, k.a);
+  }
+}
+
+// acc[row] += the chunk's entries of each row, x gathered from the slice in xs.
+template <typename VT>
+__device__ __forceinline__ void xs_compute(const XsChunk<VT>& k, const VT* __restrict__ xs, VT* __restrict__ acc,
+                                           int lane) {
+  constexpr int SB = XsCfg<VT>::kSliceBits;
+  constexpr uint32_t kMask = (1u << SB) - 1u;
+  constexpr int32_t kNone = 0x7fffffff;  // sentinel row of entries past the segment
+  int32_t rw[kXsItems];
+  VT pr[kXsItems];
+#pragma unroll
+  for (int j = 0; j < kXsItems; ++j) {
+    const bool v = j < k.nval;
+    rw[j] = v ? static_cast<int32_t>(k.id[j] >> SB) : kNone;
+    pr[j] = v ? k.a[j] * xs[k.id[j] & kMask] : VT(0);
+  }
+  // lane-local segments: a segment bounded inside the lane is the whole of the
+  // row's entries in this chunk and goes straight to its accumulator
+  VT run = VT(0), hd = VT(0);
+  bool single = true;
+#pragma unroll
+  for (int j = 0; j < kXsItems; ++j) {
+    run += pr[j];
+    if (j + 1 < kXsItems && rw[j + 1] != rw[j]) {
+      if (single)
+        hd = run;
+      else
+        acc[rw[j]] += run;  // rw[j] < kNone: a sentinel is never followed by another row
+      single = false;
+      run = VT(0);
+    }
+  }
+  const int32_t F = rw[0], R = rw[kXsItems - 1];
+  const int32_t Rprev = __shfl_up_sync(0xffffffffu, R, 1);
+  // segmented inclusive scan of the lanes' last segments
+  int flag = (lane == 0 || !single || Rprev != R) ? 1 : 0;
+  VT S = run;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const VT s_up = __shfl_up_sync(0xffffffffu, S, d);
+    const int f_up = __shfl_up_sync(0xffffffffu, flag, d);
+    if (lane >= d && !flag) S += s_up;
+    if (lane >= d) flag |= f_up;
+  }
+  const VT Sprev = __shfl_up_sync(0xffffffffu, S, 1);
+  const int32_t Fnext = __shfl_down_sync(0xffffffffu, F, 1);
+  if (!single) acc[F] += hd + ((lane > 0 && Rprev == F) ? Sprev : VT(0));
+  if (R != kNone && (lane == 31 || Fnext != R)) acc[R] += S;
+  __syncwarp();
+}
+
+// Position of a chunk in a warp's stream over the tile's slices: slice index i
+// (into tl_slice), the segment [st, st + len) and the chunk offset c; i = -1
+// past the end.  The segments of 32 slices at a time sit in the lanes
+// (lane l: slice index base + l), so finding the next slice with entries is a
+// ballot.
+struct XsPos {
+  int i;
+  int32_t st, len, c;
+};
+
+struct XsWindow {
+  int base;  // slice index held by lane 0
+  int32_t st, len;
+};
+
+__device__ __forceinline__ void xs_window_load(const XsParams& p, int64_t g, int i_end, int base, int lane,
+                                               XsWindow& w) {
+  w.base = base;
+  const int i = base + lane;
+  if (i < i_end) {
+    const int64_t key = g * p.nS + p.tl_slice[i];
+    w.st = p.seg_start[key];
+    w.len = p.seg_len[key];
+  } else {
+    w.st = 0;
+    w.len = 0;
+  }
+}
+
+// The first chunk in a slice index > i (or >= i when `from` is set) with entries.
+__device__ __forceinline__ XsPos xs_next_slice(const XsParams& p, int64_t g, int i, int i_end, int lane,
+                                               XsWindow& w) {
+  while (true) {
+    const int li = w.base + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, li > i && li < i_end && w.len > 0);
+    if (m) {
+      const int src = __ffs(m) - 1;
+      XsPos q;
+      q.i = w.base + src;
+      q.st = __shfl_sync(0xffffffffu, w.st, src);
+      q.len = __shfl_sync(0xffffffffu, w.len, src);
+      q.c = 0;
+      return q;
+    }
+    if (w.base + 32 >= i_end) return XsPos{-1, 0, 0, 0};
+    xs_window_load(p, g, i_end, w.base + 32, lane, w);
+  }
+}
+
+__device__ __forceinline__ XsPos xs_next(const XsParams& p, int64_t g, const XsPos& q, int i_end, int lane,
+                                         XsWindow& w) {
+  if (q.i < 0) return q;
+  if (q.c + kXsChunk < q.len) return XsPos{q.i, q.st, q.len, q.c + kXsChunk};
+  return xs_next_slice(p, g, q.i, i_end, lane, w);
+}
+
+template <typename VT, typename ValT>
+__global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsParams p) {
+  constexpr int S = 1 << XsCfg<VT>::kSliceBits;
+  constexpr int NX = XsCfg<VT>::kBuffers;
+  extern __shared__ __align__(128) unsigned char smem[];
+  VT* xb = reinterpret_cast<VT*>(smem);  // [NX][S]
+  VT* acc = xb + NX * S;                 // [kRows]
+  uint64_t* full = reinterpret_cast<uint64_t*>(acc + XsCfg<VT>::kRows);
+  uint64_t* empty = full + NX;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NX);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NX; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&empty[b], kXsWarps);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kXsWarps) {  // ---------------------------------------- producer
+    if (lane != 0) return;
+    const uint64_t pol = policy_evict_last();
+    uint32_t v = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; ok && t < p.ntiles; t += gridDim.x) {
+      for (int i = p.tl_off[t]; i < p.tl_off[t + 1]; ++i, ++v) {
+        const int b = v % NX;
+        if (v >= NX && !mbar_wait_bounded(&empty[b], (v / NX - 1) & 1u, p.status)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        const int64_t c0 = static_cast<int64_t>(p.tl_slice[i]) << XsCfg<VT>::kSliceBits;
+        const int width = static_cast<int>((p.N - c0 < S ? p.N - c0 : static_cast<int64_t>(S)));
+        constexpr int kVec = 16 / sizeof(VT);
+        const int wb = width / kVec * kVec;  // by bulk copy; the rest (< 16 bytes) by this thread
+        VT* dst = xb + b * S;
+        const VT* src = static_cast<const VT*>(p.x) + c0;
+        if (wb < width) {
+          for (int k = wb; k < width; ++k) dst[k] = src[k];
+          fence_proxy_async_smem();  // a later bulk copy may overwrite these addresses
+        }
+        mbar_arrive_expect_tx(&full[b], static_cast<uint32_t>(wb * sizeof(VT)));
+        if (wb > 0) bulk_g2s(dst, src, static_cast<uint32_t>(wb * sizeof(VT)), &full[b], pol);
+      }
+    }
+    // copies still in flight land before the block can exit
+    for (uint32_t u = v > NX ? v - NX : 0; u < v; ++u) mbar_wait_bounded(&full[u % NX], (u / NX) & 1u, p.status);
+    return;
+  }
+
+  // ------------------------------------------------------------- consumers
+  // Each warp keeps kDepth chunks in registers: while one is summed, the
+  // others are in flight, across slice boundaries (a warp often has one chunk
+  // per slice).  Slice i's buffer is waited for before its first chunk is
+  // summed and released after its last; slices without entries of this warp
+  // are waited for and released in turn, so every warp arrives once per slice.
+  constexpr int D = XsCfg<VT>::kDepth;
+  VT* y = static_cast<VT*>(p.y);
+  uint32_t v = 0;  // slices visited by this CTA, as counted by the producer
+  bool ok = true;
+  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+    const int32_t tr0 = p.tile_row[t];
+    const int64_t g = static_cast<int64_t>(t) * kXsWarps + warp;
+    const int32_t r_lo = p.warp_row[g] - tr0, r_hi = p.warp_row[g + 1] - tr0;
+    const int i0 = p.tl_off[t], i1 = p.tl_off[t + 1];
+    for (int32_t r = r_lo + lane; r < r_hi; r += 32) acc[r] = VT(0);
+    __syncwarp();
+    XsWindow win;
+    xs_window_load(p, g, i1, i0, lane, win);
+    XsPos q[D];
+    XsChunk<VT> k[D];
+    q[0] = xs_next_slice(p, g, i0 - 1, i1, lane, win);
+#pragma unroll
+    for (int d = 1; d < D; ++d) q[d] = xs_next(p, g, q[d - 1], i1, lane, win);
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      if (q[d].i >= 0) xs_load<VT, ValT>(p, q[d].st, q[d].len, q[d].c, lane, k[d]);
+    int i = i0;           // next slice to wait for
+    bool held = false;    // slice i - 1 is waited for and not yet released
+    while (q[0].i >= 0) {
+      const XsChunk<VT> cur = k[0];
+      const XsPos qc = q[0];
+#pragma unroll
+      for (int d = 0; d + 1 < D; ++d) {
+        k[d] = k[d + 1];
+        q[d] = q[d + 1];
+      }
+      q[D - 1] = xs_next(p, g, q[D - 1], i1, lane, win);
+      if (q[D - 1].i >= 0) xs_load<VT, ValT>(p, q[D - 1].st, q[D - 1].len, q[D - 1].c, lane, k[D - 1]);
+      while (i <= qc.i) {  // wait for slices up to this chunk's, releasing the empty ones
+        if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
+        if (ok) {
+          ok = mbar_wait_bounded(&full[v % NX], (v / NX) & 1u, p.status);
+          ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+          if (!ok) *abort_flag = 1;
+        }
+        held = true;
+        ++i;
+        ++v;
+      }
+      if (ok) xs_compute<VT>(cur, xb + ((v - 1) % NX) * S, acc, lane);
+    }
+    while (i < i1) {  // slices after this warp's last entries
+      if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
+      if (ok) {
+        ok = mbar_wait_bounded(&full[v % NX], (v / NX) & 1u, p.status);
+        ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+        if (!ok) *abort_flag = 1;
+      }
+      held = true;
+      ++i;
+      ++v;
+    }
+    if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
+    __syncwarp();
+    if (ok)
+      for (int32_t r = r_lo + lane; r < r_hi; r += 32) {
+        const int32_t row = tr0 + r;
+        y[p.yperm ? p.yperm[row] : row] = acc[r];
+      }
+    named_bar(1, 32 * kXsWarps);  // the next tile re-partitions the accumulators
+  }
+}
+
+// ------------------------------------------------------------- building
+
+// keys[e] = (row << 32) | (warp range * nS + slice); counts per (warp range, slice).
+__global__ void xs_key_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t M,
+                              int64_t Z, const int32_t* __restrict__ warp_row, int32_t G, int32_t nS, int sbits,
+                              uint64_t* __restrict__ keys, int32_t* __restrict__ vals, int32_t* __restrict__ counts) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= Z) return;
+  int32_t lo = 0, hi = M;  // row: last i with rowptr[i] <= e
+  while (hi - lo > 1) {
+    const int32_t mid = lo + (hi - lo) / 2;
+    if (rowptr[mid] <= e)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  int32_t glo = 0, ghi = G;  // warp range: last g with warp_row[g] <= row
+  while (ghi - glo > 1) {
+    const int32_t mid = glo + (ghi - glo) / 2;
+    if (warp_row[mid] <= lo)
+      glo = mid;
+    else
+      ghi = mid;
+  }
+  const uint32_t key = static_cast<uint32_t>(glo) * static_cast<uint32_t>(nS) + static_cast<uint32_t>(col[e] >> sbits);
+  keys[e] = (static_cast<uint64_t>(static_cast<uint32_t>(lo)) << 32) | key;
+  vals[e] = static_cast<int32_t>(e);
+  atomicAdd(counts + key, 1);
+}
+
+// Place sorted entry i at seg_start[key] + (i - first sorted index of key).
+__global__ void xs_scatter_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals, int64_t Z,
+                                  const int32_t* __restrict__ seg_start, const int32_t* __restrict__ ustart,
+                                  const int32_t* __restrict__ col, const void* __restrict__ val, int vbytes,
+                                  const int32_t* __restrict__ tile_row, int sbits, int32_t nS,
+                                  uint32_t* __restrict__ idx_out, void* __restrict__ val_out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= Z) return;
+  const uint64_t k = keys[i];
+  const uint32_t key = static_cast<uint32_t>(k);
+  const int32_t row = static_cast<int32_t>(k >> 32);
+  const int32_t e = vals[i];
+  const int32_t g = static_cast<int32_t>(key / static_cast<uint32_t>(nS));
+  const int32_t t = g / kXsWarps;
+  const int64_t pos = static_cast<int64_t>(seg_start[key]) + (i - ustart[key]);
+  idx_out[pos] = (static_cast<uint32_t>(row - tile_row[t]) << sbits) | (static_cast<uint32_t>(col[e]) & ((1u << sbits) - 1u));
+  if (vbytes == 8)
+    static_cast<double*>(val_out)[pos] = static_cast<const double*>(val)[e];
+  else if (vbytes == 4)
+    static_cast<float*>(val_out)[pos] = static_cast<const float*>(val)[e];
+  else
+    static_cast<uint16_t*>(val_out)[pos] = static_cast<const uint16_t*>(val)[e];
+}
+
+int bit_width_u64(uint64_t v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+template <typename VT, typename ValT>
+maxe_status xs_launch(const maxe_handle* h, const void* x, void* y, const int32_t* yperm, cudaStream_t st) {
+  static bool attr_set[64] = {};
+  if (h->device >= 0 && h->device < 64 && !attr_set[h->device]) {
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmv_xslice_kernel<VT, ValT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(xs_smem_bytes<VT>())));
+    attr_set[h->device] = true;
+  }
+  XsParams p{};
+  p.idx = h->xs_idx;
+  p.val = h->xs_val;
+  p.seg_start = h->xs_seg_start;
+  p.seg_len = h->xs_seg_len;
+  p.tile_row = h->xs_tile_row;
+  p.warp_row = h->xs_warp_row;
+  p.tl_off = h->xs_tl_off;
+  p.tl_slice = h->xs_tl_slice;
+  p.ntiles = h->xs_ntiles;
+  p.nS = h->xs_nS;
+  p.N = h->cols;
+  p.x = x;
+  p.y = y;
+  p.yperm = yperm;
+  p.status = h->status;
+  const int grid = std::min(h->xs_ntiles, h->sms);
+  spmv_xslice_kernel<VT, ValT><<<grid, kXsThreads, xs_smem_bytes<VT>(), st>>>(p);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  return MAXE_OK;
+}
+
+template <typename VT>
+maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool* built) {
+  constexpr int SB = XsCfg<VT>::kSliceBits;
+  constexpr int RMAX = XsCfg<VT>::kRows;
+  *built = false;
+  const int32_t M = h->rows, N = h->cols;
+  const int64_t Z = h->nnz;
+  if (M == 0 || N == 0 || Z == 0) return MAXE_OK;
+  const int vb = value_bytes(h->dtype);
+  // ---- tiles and warp ranges, on the host from rowptr
+  std::vector<int32_t> rp(static_cast<size_t>(M) + 1);
+  MAXE_CUDA_TRY(cudaMemcpyAsync(rp.data(), h->rowptr, sizeof(int32_t) * (M + 1), cudaMemcpyDeviceToHost, st));
+  MAXE_CUDA_TRY(cudaStreamSynchronize(st));
+  const int64_t Ht = std::max<int64_t>(1, ceil_div(Z, std::max(h->sms, 1)));
+  std::vector<int32_t> trow{0}, wrow;
+  for (int32_t r = 0; r < M;) {
+    const int64_t target = rp[r] + Ht;
+    int32_t r2 = static_cast<int32_t>(std::lower_bound(rp.begin() + r + 1, rp.end(), target) - rp.begin());
+    r2 = std::min<int64_t>({static_cast<int64_t>(r2), static_cast<int64_t>(r) + RMAX, static_cast<int64_t>(M)});
+    r2 = std::max(r2, r + 1);
+    trow.push_back(r2);
+    r = r2;
+  }
+  const int32_t ntiles = static_cast<int32_t>(trow.size()) - 1;
+  for (int32_t t = 0; t < ntiles; ++t) {
+    const int32_t a = trow[t], b = trow[t + 1];
+    const int64_t E = static_cast<int64_t>(rp[b]) - rp[a];
+    int32_t prev = a;
+    for (int w = 0; w < kXsWarps; ++w) {
+      int32_t r = a;
+      if (w > 0) {
+        const int64_t target = rp[a] + (E * w + kXsWarps - 1) / kXsWarps;
+        r = static_cast<int32_t>(std::lower_bound(rp.begin() + a, rp.begin() + b + 1, target) - rp.begin());
+        r = std::min(std::max(r, prev), b);
+      }
+      wrow.push_back(r);
+      prev = r;
+    }
+  }
+  wrow.push_back(M);
+  const int64_t G = static_cast<int64_t>(ntiles) * kXsWarps;
+  const int32_t nS = static_cast<int32_t>(ceil_div(N, int64_t(1) << SB));
+  if (G * nS > (int64_t(1) << 24)) return MAXE_OK;  // too many (warp range, slice) cells to plan
+  const int64_t matrix_bytes = Z * (vb + 4);
+
+  const Allocator& al = h->al;
+  ScratchSet scratch(al);
+  int32_t* d_wrow = static_cast<int32_t*>(al.get(sizeof(int32_t) * (G + 1)));
+  int32_t* d_trow = static_cast<int32_t*>(al.get(sizeof(int32_t) * (ntiles + 1)));
+  if (!d_wrow || !d_trow) {
+    al.put(d_wrow);
+    al.put(d_trow);
+    return MAXE_ERR_OOM;
+  }
+  auto fail = [&](maxe_status s) {
+    al.put(d_wrow);
+    al.put(d_trow);
+    return s;
+  };
+  MAXE_CUDA_TRY(cudaMemcpyAsync(d_wrow, wrow.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, st));
+  MAXE_CUDA_TRY(cudaMemcpyAsync(d_trow, trow.data(), sizeof(int32_t) * (ntiles + 1), cudaMemcpyHostToDevice, st));
+  // ---- keys and counts
+  const int64_t cells = G * nS;
+  uint64_t* keys = scratch.get<uint64_t>(Z);
+  uint64_t* keys_alt = scratch.get<uint64_t>(Z);
+  int32_t* vals = scratch.get<int32_t>(Z);
+  int32_t* vals_alt = scratch.get<int32_t>(Z);
+  int32_t* counts = scratch.get<int32_t>(cells);
+  void* rs = scratch.get<unsigned char>(radix_scratch_bytes(Z));
+  if (!keys || !keys_alt || !vals || !vals_alt || !counts || !rs) return fail(MAXE_ERR_OOM);
+  MAXE_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * cells, st));
+  xs_key_kernel<<<static_cast<unsigned>(ceil_div(Z, 256)), 256, 0, st>>>(h->rowptr, h->col, M, Z, d_wrow,
+                                                                         static_cast<int32_t>(G), nS, SB, keys, vals,
+                                                                         counts);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  std::vector<int32_t> cnt(static_cast<size_t>(cells));
+  MAXE_CUDA_TRY(cudaMemcpyAsync(cnt.data(), counts, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, st));
+  MAXE_CUDA_TRY(cudaStreamSynchronize(st));
+  // ---- segment layout, slices per tile, the traffic estimate
+  std::vector<int32_t> seg_start(static_cast<size_t>(cells)), ustart(static_cast<size_t>(cells));
+  std::vector<int32_t> tl_off{0}, tl_slice;
+  int64_t pos = 0, upos = 0;
+  for (int64_t k = 0; k < cells; ++k) {
+    seg_start[k] = static_cast<int32_t>(pos);
+    ustart[k] = static_cast<int32_t>(upos);
+    pos += round_up(cnt[k], kXsAlign);
+    upos += cnt[k];
+  }
+  const int64_t Zp = pos;
+  if (Zp + kXsSlack > INT32_MAX) return fail(MAXE_OK);
+  for (int32_t t = 0; t < ntiles; ++t) {
+    for (int32_t s = 0; s < nS; ++s) {
+      int64_t any = 0;
+      for (int w = 0; w < kXsWarps; ++w) any += cnt[(static_cast<int64_t>(t) * kXsWarps + w) * nS + s];
+      if (any) tl_slice.push_back(s);
+    }
+    tl_off.push_back(static_cast<int32_t>(tl_slice.size()));
+  }
+  const int64_t x_bytes = static_cast<int64_t>(tl_slice.size()) * sizeof(VT) * (int64_t(1) << SB);
+  if (!force && x_bytes > 4 * matrix_bytes) return fail(MAXE_OK);  // the CSR kernel will do better
+  // ---- device arrays of the format
+  uint32_t* idx = static_cast<uint32_t*>(al.get(sizeof(uint32_t) * (Zp + kXsSlack)));
+  void* xval = al.get(static_cast<size_t>(vb) * (Zp + kXsSlack));
+  int32_t* d_seg = static_cast<int32_t*>(al.get(sizeof(int32_t) * 2 * cells));
+  int32_t* d_ustart = scratch.get<int32_t>(cells);
+  int32_t* d_tl = static_cast<int32_t*>(al.get(sizeof(int32_t) * (tl_off.size() + std::max<size_t>(tl_slice.size(), 1))));
+  if (!idx || !xval || !d_seg || !d_ustart || !d_tl) {
+    al.put(idx);
+    al.put(xval);
+    al.put(d_seg);
+    al.put(d_tl);
+    return fail(MAXE_ERR_OOM);
+  }
+  int32_t* d_len = d_seg + cells;
+  MAXE_CUDA_TRY(cudaMemcpyAsync(d_seg, seg_start.data(), sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
+  MAXE_CUDA_TRY(cudaMemcpyAsync(d_len, cnt.data(), sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
+  MAXE_CUDA_TRY(cudaMemcpyAsync(d_ustart, ustart.data(), sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
+  MAXE_CUDA_TRY(cudaMemcpyAsync(d_tl, tl_off.data(), sizeof(int32_t) * tl_off.size(), cudaMemcpyHostToDevice, st));
+  if (!tl_slice.empty())
+    MAXE_CUDA_TRY(cudaMemcpyAsync(d_tl + tl_off.size(), tl_slice.data(), sizeof(int32_t) * tl_slice.size(),
+                                  cudaMemcpyHostToDevice, st));
+  MAXE_CUDA_TRY(cudaMemsetAsync(idx, 0, sizeof(uint32_t) * (Zp + kXsSlack), st));
+  MAXE_CUDA_TRY(cudaMemsetAsync(xval, 0, static_cast<size_t>(vb) * (Zp + kXsSlack), st));
+  // ---- stable sort by (warp range, slice); entries keep CSR order inside a cell
+  MAXE_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, Z, bit_width_u64(static_cast<uint64_t>(cells - 1)), rs,
+                            st));
+  xs_scatter_kernel<<<static_cast<unsigned>(ceil_div(Z, 256)), 256, 0, st>>>(
+      keys, vals, Z, d_seg, d_ustart, h->col, h->val, vb, d_trow, SB, nS, idx, xval);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  MAXE_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors and scratch go out of scope
+  h->xs_idx = idx;
+  h->xs_val = xval;
+  h->xs_seg_start = d_seg;
+  h->xs_seg_len = d_len;
+  h->xs_tile_row = d_trow;
+  h->xs_warp_row = d_wrow;
+  h->xs_tl_off = d_tl;
+  h->xs_tl_slice = d_tl + tl_off.size();
+  h->xs_ntiles = ntiles;
+  h->xs_nS = nS;
+  h->xs_bytes = static_cast<int64_t>(Zp) * (4 + vb);
+  *built = true;
+  return MAXE_OK;
+}
+
+}  // namespace
+
+maxe_status xslice_build(maxe_handle* h, cudaStream_t st, bool force) {
+  bool built = false;
+  maxe_status s = h->dtype == MAXE_F64 ? build<double>(h, st, force, &built) : build<float>(h, st, force, &built);
+  if (s == MAXE_OK && built) h->xs_use = 1;
+  return s;
+}
+
+bool xslice_ready(const maxe_handle* h, const void* x) {
+  return h->xs_idx && h->xs_use && (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+}
+
+maxe_status xslice_launch(const maxe_handle* h, const void* x, void* y, const int32_t* yperm, cudaStream_t st) {
+  if (h->dtype == MAXE_F64) return xs_launch<double, double>(h, x, y, yperm, st);
+  if (h->dtype == MAXE_F32) return xs_launch<float, float>(h, x, y, yperm, st);
+  return xs_launch<float, uint16_t>(h, x, y, yperm, st);
+}
+
+void xslice_release(maxe_handle* h) {
+  const Allocator& al = h->al;
+  al.put(h->xs_tl_off);
+  al.put(h->xs_seg_start);
+  al.put(h->xs_val);
+  al.put(h->xs_idx);
+  al.put(h->xs_warp_row);
+  al.put(h->xs_tile_row);
+  h->xs_tl_off = h->xs_tl_slice = h->xs_seg_start = h->xs_seg_len = nullptr;
+  h->xs_warp_row = h->xs_tile_row = nullptr;
+  h->xs_idx = nullptr;
+  h->xs_val = nullptr;
+  h->xs_use = 0;
+}
+
+}  // namespace maxe

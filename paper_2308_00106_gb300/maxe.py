@@ -28,6 +28,7 @@ MAXE_ITEMS16 = 0x8
 MAXE_SPMM_LANES = 0x10
 MAXE_EQUAL_ROWS = 0x20
 MAXE_COO = 0x40
+MAXE_XSLICE = 0x80
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -230,6 +231,10 @@ class Handle:
         """Entries per lane of the SpMV kernel variant this handle uses (8 or 16)."""
         return self._tuning() & 0xFF
 
+    def xslice(self) -> bool:
+        """True when SpMV runs on the x-sliced form (MAXE_XSLICE, kept by the autotuner or forced)."""
+        return bool(self._tuning() & 0x200)
+
     def spmm_lanes(self) -> bool:
         """True when SpMM spreads the k columns across lanes (else column passes)."""
         return bool(self._tuning() & 0x100)
@@ -293,7 +298,7 @@ def maxe_permute_scatter(perm: torch.Tensor, y: torch.Tensor, stream=None):
 def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
                      stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False,
-                     equal_rows: bool = False, coo: bool = False) -> Handle:
+                     equal_rows: bool = False, coo: bool = False, xslice: bool = False) -> Handle:
     """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity."""
     code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[val.dtype]
     _dev(rowptr, torch.int32, "rowptr")
@@ -308,7 +313,7 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
     out = ctypes.c_void_p()
     flags = ((MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
              | (MAXE_SPMM_LANES if spmm_lanes else 0) | (MAXE_EQUAL_ROWS if equal_rows else 0)
-             | (MAXE_COO if coo else 0))
+             | (MAXE_COO if coo else 0) | (MAXE_XSLICE if xslice else 0))
     _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
@@ -385,10 +390,10 @@ def maxe_version() -> str:
 
 
 def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False,
-             spmm_lanes=False, equal_rows=False, coo=False) -> Handle:
+             spmm_lanes=False, equal_rows=False, coo=False, xslice=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
     return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16,
-                            spmm_lanes, equal_rows, coo)
+                            spmm_lanes, equal_rows, coo, xslice)
 
 
 class Batch:

@@ -1,0 +1,105 @@
+"""GPU parity of the x-sliced SpMV (x staged in shared memory by column slices,
+rows owned by warps): products within the FP tolerance of the FP64 oracle in
+both spaces, deterministic, with tiles looping over CTAs, and the CSR kernel
+taking over for unaligned x."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_00106_gb300 import maxe
+from paper_2308_00106_gb300 import workloads as W
+from tests.gpu_common import EDGE_KINDS, TOL, code, edge_matrix, oracle_permuted, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    maxe.load(build_if_missing=True)
+
+
+def _perms(A, seed):
+    return maxe.maxe_build_permutation(seed, A.rows, 0), maxe.maxe_build_permutation(seed, A.cols, 1)
+
+
+@pytest.mark.parametrize("kind", EDGE_KINDS + ["mixed"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_xslice_spmv_against_oracle(kind, dtype):
+    if kind == "mixed":
+        L = np.random.default_rng(7).choice([0, 1, 7, 8, 9, 255, 256, 257, 900], 3000)
+        A = W.from_lengths(7, L, 40000, dtype)
+    else:
+        A = edge_matrix(kind, dtype, seed=8)
+    rperm, cperm = _perms(A, 31)
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, xslice=True)
+    assert h.xslice() == (A.nnz > 0)
+    vd = "f64" if dtype == "f64" else "f32"
+    x = W.vector(9, A.cols, vd, "cuda")
+    rp, co, va = A.numpy()
+    y = torch.full((A.rows,), float("nan"), dtype=x.dtype, device="cuda")
+    maxe.maxe_spmv(h, x, y)  # original space: x gathered, y scattered through rperm
+    assert not torch.isnan(y).any()
+    assert rel_l2(y.cpu().numpy(), oracle.spmv(A.rows, rp, co, va, code(dtype), x.cpu().numpy())) <= TOL[dtype]
+    nrp, nco, nva = oracle_permuted(A, rperm, cperm)
+    xp = x[cperm.long()].contiguous()
+    yp = maxe.maxe_spmv(h, xp, permuted=True)
+    assert rel_l2(yp.cpu().numpy(), oracle.spmv(A.rows, nrp, nco, nva, code(dtype), xp.cpu().numpy())) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_xslice_many_tiles_per_cta(dtype):
+    """More row tiles than SMs (the 5-point Laplacian, 2.9M rows): CTAs loop over
+    tiles and the slice ring's phases carry across them."""
+    A = W.laplacian5(1700, dtype, "cuda")
+    h = maxe.from_csr(A, xslice=True)
+    assert h.xslice()
+    x = W.vector(3, A.cols, dtype, "cuda")
+    y = maxe.maxe_spmv(h, x)
+    rp, co, va = A.numpy()
+    rows = np.random.default_rng(1).choice(A.rows, 4000, replace=False)
+    ref = oracle.spmv_rows(rp, co, va, code(dtype), x.cpu().numpy(), rows)
+    assert rel_l2(y.cpu().numpy()[rows], ref) <= TOL[dtype]
+    ones = maxe.maxe_spmv(h, torch.ones(A.cols, dtype=x.dtype, device="cuda")).cpu().numpy().reshape(1700, 1700)
+    ref1 = np.zeros((1700, 1700))
+    ref1[0, :] += 1
+    ref1[-1, :] += 1
+    ref1[:, 0] += 1
+    ref1[:, -1] += 1
+    np.testing.assert_array_equal(ones, ref1)
+
+
+def test_xslice_powerlaw_deterministic_and_matches_csr():
+    A = W.powerlaw(5, n=400000, device="cuda")
+    rperm, cperm = _perms(A, 5)
+    h = maxe.from_csr(A, rperm, cperm, xslice=True)
+    hc = maxe.from_csr(A, rperm, cperm)
+    assert h.xslice() and not hc.xslice()
+    x = W.vector(4, A.cols, "f32", "cuda")
+    y1 = maxe.maxe_spmv(h, x)
+    assert torch.equal(maxe.maxe_spmv(h, x), y1)
+    assert rel_l2(y1.cpu().numpy(), maxe.maxe_spmv(hc, x).cpu().numpy()) <= 1e-6
+    rp, co, va = A.numpy()
+    rows = np.random.default_rng(2).choice(A.rows, 3000, replace=False)
+    assert rel_l2(y1.cpu().numpy()[rows], oracle.spmv_rows(rp, co, va, code("f32"), x.cpu().numpy(), rows)) <= TOL["f32"]
+    # x not 16-byte aligned: the CSR kernel runs instead, same result within FP32 rounding
+    xb = torch.empty(A.cols + 1, device="cuda")
+    xb[1:] = x[cperm.long()]
+    yu = maxe.maxe_spmv(h, xb[1:], permuted=True)
+    ya = maxe.maxe_spmv(h, x[cperm.long()].contiguous(), permuted=True)
+    assert rel_l2(yu.cpu().numpy(), ya.cpu().numpy()) <= 1e-6
+    # the power iteration runs its products through the same kernel
+    v0 = W.vector(8, A.rows, "f32", "cuda")
+    lam_x, _ = maxe.maxe_power_iteration(h, v0, 5)
+    lam_c, _ = maxe.maxe_power_iteration(hc, v0, 5)
+    assert abs(lam_x - lam_c) <= 1e-4 * abs(lam_c)
+
+
+def test_xslice_autotune_keeps_the_faster_kernel():
+    A = W.powerlaw(6, n=300000, device="cuda")
+    h = maxe.from_csr(A, *_perms(A, 6), autotune=True)
+    x = W.vector(5, A.cols, "f32", "cuda")
+    rp, co, va = A.numpy()
+    rows = np.random.default_rng(3).choice(A.rows, 2000, replace=False)
+    y = maxe.maxe_spmv(h, x)
+    assert rel_l2(y.cpu().numpy()[rows], oracle.spmv_rows(rp, co, va, code("f32"), x.cpu().numpy(), rows)) <= TOL["f32"]
