@@ -62,7 +62,9 @@ def traffic_from_profile(name):
     return t, kernel_rev
 
 
-KERNEL_REVISION = "spmm_warp_kernel r3"  # bump whenever the SpMV kernel changes
+# bump a revision whenever that kernel changes: its committed ncu traffic then no longer applies
+KERNEL_REVISION = {"spmm_warp_kernel": "spmm_warp_kernel r3", "spmv_xslice_kernel": "spmv_xslice_kernel r1"}
+PROFILE_OF = {"spmm_warp_kernel": "spmv_warp_powerlaw1M_f32.md", "spmv_xslice_kernel": "spmv_xslice_powerlaw1M_f32.md"}
 
 
 class Clocks:
@@ -648,6 +650,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="batched workload: default batch plans, no autotuning")
     ap.add_argument("--items-per-lane", choices=["auto", "8", "16"], default="auto",
                     help="SpMV kernel variant: autotuned per handle, or fixed")
+    ap.add_argument("--xslice", action="store_true",
+                    help="SpMV on the x-sliced form for both handles (no autotuning); for profiling that kernel")
     ap.add_argument("--seed", type=int, default=2308)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -688,11 +692,11 @@ def main():
     rperm = maxe.maxe_build_permutation(args.seed, M, 0)
     cperm = maxe.maxe_build_permutation(args.seed, N, 1)
     ev[1].record()
-    tune = args.items_per_lane == "auto"
+    tune = args.items_per_lane == "auto" and not args.xslice
     i16 = args.items_per_lane == "16"
-    hP = maxe.from_csr(A, rperm, cperm, autotune=tune, items16=i16)
+    hP = maxe.from_csr(A, rperm, cperm, autotune=tune, items16=i16, xslice=args.xslice)
     ev[2].record()
-    hN = maxe.from_csr(A, autotune=tune, items16=i16)
+    hN = maxe.from_csr(A, autotune=tune, items16=i16, xslice=args.xslice)
     ev[3].record()
     torch.cuda.synchronize()
     t_perm, t_pcsr = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
@@ -760,8 +764,9 @@ def main():
     ms_e2e = timed_steps(step_e2e, max(args.steps // 4, 1), args.warmup, world, graph_len=1)
     e2e_gbs = bytes_step / (ms_e2e * 1e-3) / 1e9
 
-    traffic, rev = traffic_from_profile("spmv_warp_powerlaw1M_f32.md")
-    if rev != KERNEL_REVISION:
+    kern = "spmv_xslice_kernel" if hP.xslice() else "spmm_warp_kernel"
+    traffic, rev = traffic_from_profile(PROFILE_OF[kern])
+    if rev != KERNEL_REVISION[kern]:
         traffic = None
 
     out = {
@@ -789,7 +794,7 @@ def main():
         "spot_rel_l2_vs_oracle": spot_err,
         "roofline": {"bound": "hbm", "achieved": round(gbs, 3), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "traffic": traffic, "peak_source": src,
-                     "bytes_per_launch": bytes_step},
+                     "bytes_per_launch": bytes_step, "kernel": kern},
         "e2e": {"value": round(e2e_gbs * world, 3), "unit": "GB/s", "h2d_bytes_per_step": N * xb,
                 "d2h_bytes_per_step": M * xb, "ms_per_step": ms_e2e},
         "gpu_launches": args.steps,
