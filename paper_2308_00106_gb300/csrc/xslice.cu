@@ -47,7 +47,7 @@ struct XsCfg<float> {
   static constexpr int kSliceBits = 14;  // 16384 columns, 64 KB
   static constexpr int kBuffers = 3;     // slices in the ring: two loads in flight while one is read
   static constexpr int kRows = 8192;     // rows per tile, 32 KB of accumulators
-  static constexpr int kDepth = 3;       // chunks per warp in registers (one summed, the rest in flight)
+  static constexpr int kDepth = 2;       // chunks per warp in registers (one summed, one in flight)
 };
 template <>
 struct XsCfg<double> {
@@ -119,12 +119,16 @@ template <>
 struct XsVals<uint16_t> {  // BF16 values, FP32 arithmetic
   using AT = float;
   static __device__ __forceinline__ void load(const void* v, int64_t e, float (&a)[kXsItems]) {
-    const uint4 t = __ldcs(reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(v) + e));
-    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(v) + e);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      a[2 * q] = __uint_as_float(w[q] << 16);
-      a[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+    for (int h = 0; h < kXsItems / 8; ++h) {
+      const uint4 t = __ldcs(p + h);
+      const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[8 * h + 2 * q] = __uint_as_float(w[q] << 16);
+        a[8 * h + 2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+      }
     }
   }
 };
@@ -144,9 +148,11 @@ __device__ __forceinline__ void xs_load(const XsParams& p, int32_t st, int32_t l
   k.nval = min(kXsItems, len - off);
   if (k.nval > 0) {
     const uint4* ip = reinterpret_cast<const uint4*>(p.idx + st + off);
-    const uint4 u0 = __ldcs(ip), u1 = __ldcs(ip + 1);
-    k.id[0] = u0.x, k.id[1] = u0.y, k.id[2] = u0.z, k.id[3] = u0.w;
-    k.id[4] = u1.x, k.id[5] = u1.y, k.id[6] = u1.z, k.id[7] = u1.w;
+#pragma unroll
+    for (int q = 0; q < kXsItems / 4; ++q) {
+      const uint4 u = __ldcs(ip + q);
+      k.id[4 * q] = u.x, k.id[4 * q + 1] = u.y, k.id[4 * q + 2] = u.z, k.id[4 * q + 3] = u.w;
+    }
     XsVals<ValT>::load(p.val, static_cast<int64_t>(st) + off, k.a);
   }
 }
