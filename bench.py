@@ -158,6 +158,9 @@ def make_workload(name, seed, device):
     if name == "blockdiag":
         return W.blockdiag(seed, device=device), "f64", (
             "4096x4096, 16 diagonal 256x256 blocks at 2% fill + 2000 off-block entries, FP64")
+    if name == "clustered":
+        return W.clustered_heavy(seed, 1 << 20, dtype="f32", device=device), "f32", (
+            "1048576x1048576, first 1% of rows 1000 entries, the rest 16, distinct uniform columns, FP32")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -259,15 +262,53 @@ def run_reference(args):
     vb = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
     xb = 8 if dtype == "f64" else 4
     z1 = int(prp[r1])
+    cores = 1
+    pool = None
+    if args.cpu_workers > 1:
+        # the paper's parallel CPU CSR (Section 6): rows split into equal-row
+        # ranges, one per worker; here threads (the oracle's C call releases the
+        # GIL), the same sample of rows, natural order and permuted order
+        import concurrent.futures as cf
+        nw = args.cpu_workers
+
+        def ranges(rp_, co_, va_):
+            cuts = [r1 * w // nw for w in range(nw + 1)]
+            out = []
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                e0, e1 = int(rp_[a]), int(rp_[b])
+                out.append((b - a, (rp_[a:b + 1] - e0).astype(np.int32), co_[e0:e1], va_[e0:e1]))
+            return out
+
+        def timed_pool(parts):
+            with cf.ThreadPoolExecutor(nw) as ex:
+                run = lambda: list(ex.map(lambda q: oracle.spmv(q[0], q[1], q[2], q[3], code, x), parts))  # noqa: E731
+                for _ in range(args.warmup):
+                    run()
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    run()
+                return (time.perf_counter() - t0) / args.steps
+
+        dt_perm = timed_pool(ranges(prp, pco, pva))
+        dt_nat = timed_pool(ranges(rp, co, va))
+        z_nat = int(rp[r1])
+        pool = {"workers": nw, "split": "equal rows", "permuted_ms": dt_perm * 1e3, "natural_ms": dt_nat * 1e3,
+                "natural_gbs": round(alg_bytes(r1, N, z_nat, vb, xb, xb) / dt_nat / 1e9, 4),
+                "permuted_over_natural_speed": round(dt_nat / dt_perm * (z1 / max(z_nat, 1)), 4)}
+        dt = dt_perm
+        cores = nw
     gbs = alg_bytes(r1, N, z1, vb, xb, xb) / dt / 1e9
     sample = f"rows 0..{r1} of the permuted matrix ({z1} of {Z} nonzeros) per step"
+    if pool:
+        sample += f", split into {pool['workers']} equal-row ranges on as many threads"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "variant": "permuted R-C, vectors in permuted space"},
-        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        **({"equal_rows_pool": pool} if pool else {}),
     }))
 
 
@@ -642,7 +683,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["maxe", "reference"], default="maxe")
-    ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag", "batched", "serving",
+    ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag", "clustered", "batched", "serving",
                                            "laplacian-table", "partition-table", "shuffle-table"],
                     default="powerlaw")
     ap.add_argument("--requests", type=int, default=1500, help="requests per serving trace")
@@ -654,6 +695,9 @@ def main():
                     help="SpMV on the x-sliced form for both handles (no autotuning); for profiling that kernel")
     ap.add_argument("--seed", type=int, default=2308)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-workers", type=int, default=1,
+                    help="reference arm: split the oracle's product into this many equal-row ranges on threads "
+                         "(the paper's parallel CPU CSR), timed for the natural and the permuted matrix")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph-len", type=int, default=50)
     ap.add_argument("--profile", action="store_true",
