@@ -208,6 +208,43 @@ def timed_steps(step, K, W, world, graph_len=50):
     return max_over_ranks(ms, world) / K
 
 
+def seed_sweep(A, x, args, world, tune):
+    """The paper's protocol (32 runs with different permutations): permuted SpMV
+    for seeds 0..n-1, each with its own handle (built as in the timed run),
+    GB/s min / mean / max, the 64x64-grid entropy per seed, and the cold first
+    launch of the first seed (right after its handle is built, L2 flushed)."""
+    from paper_2308_00106_gb300 import maxe
+    M, N = A.rows, A.cols
+    vb = {torch.float64: 8, torch.float32: 4, torch.bfloat16: 2}[A.val.dtype]
+    xb = 8 if vb == 8 else 4
+    by = alg_bytes(M, N, A.nnz, vb, xb, xb)
+    gbs, ents, cold = [], [], None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for sd in range(args.seeds):
+        r = maxe.maxe_build_permutation(sd, M, 0)
+        c = maxe.maxe_build_permutation(sd, N, 1)
+        h = maxe.from_csr(A, r, c, autotune=tune)
+        xp = x[c.long()].contiguous()
+        y = torch.empty(M, dtype=xp.dtype, device="cuda")
+        if sd == 0:
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            maxe.maxe_spmv(h, xp, y, permuted=True)
+            e1.record()
+            torch.cuda.synchronize()
+            cold = e0.elapsed_time(e1)
+        ms = timed_steps(lambda: maxe.maxe_spmv(h, xp, y, permuted=True), 200, 3, world, graph_len=50)
+        gbs.append(by / (ms * 1e-3) / 1e9)
+        ents.append(maxe.maxe_nnz_entropy(h, 64, 64, counts=False)[0])
+        h.close()
+    del flush
+    return {"n": args.seeds, "gbs_min": round(min(gbs), 3), "gbs_mean": round(float(np.mean(gbs)), 3),
+            "gbs_max": round(max(gbs), 3), "entropy_64x64_min": round(min(ents), 4),
+            "entropy_64x64_max": round(max(ents), 4), "cold_first_launch_ms": cold,
+            "what": "seeds 0..n-1 for the row and column permutations; 200 products each (CUDA graph)"}
+
+
 def timed_streams(step, streams, K, W, world):
     """W warm-up steps, then exactly K steps step(k) that spread over `streams`;
     device time from an event before the first to one after all streams drain
@@ -233,7 +270,7 @@ def timed_streams(step, streams, K, W, world):
 
 
 def flushed_launch_ms(step, reps=20):
-    """Mean device time of one launch with L2 flushed (256 MB write) before each."""
+    """Median device time of one launch with L2 flushed (256 MB write) before each."""
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     times = []
     for _ in range(reps):
@@ -246,6 +283,30 @@ def flushed_launch_ms(step, reps=20):
         times.append(a.elapsed_time(b))
     del flush
     return statistics.median(times)
+
+
+def host_info() -> dict:
+    """CPU model and core count of the machine the CPU numbers come from."""
+    import platform
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
 
 
 def cpu_baseline(A, x_np, code, seconds=10.0):
@@ -339,7 +400,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "variant": "permuted R-C, vectors in permuted space"},
-        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         **({"equal_rows_pool": pool} if pool else {}),
     }))
@@ -702,6 +764,7 @@ def main():
                          "(the paper's parallel CPU CSR), timed for the natural and the permuted matrix")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph-len", type=int, default=50)
+    ap.add_argument("--seeds", type=int, default=32, help="permutation seeds of the min/mean/max sweep (0: skip)")
     ap.add_argument("--profile", action="store_true",
                     help="no timing: 3 permuted then 3 plain SpMV launches (for an ncu capture)")
     args = ap.parse_args()
@@ -778,8 +841,9 @@ def main():
     clk = clocks.stop()
     ms_plain = timed_steps(step_plain, args.steps, args.warmup, world, args.graph_len)
     ms_full = timed_steps(step_full, max(args.steps // 4, 1), args.warmup, world, args.graph_len)
-    fl_perm = flushed_launch_ms(step_perm)
-    fl_plain = flushed_launch_ms(step_plain)
+    fl_perm = flushed_launch_ms(step_perm, reps=200)
+    fl_plain = flushed_launch_ms(step_plain, reps=200)
+    seeds = seed_sweep(A, x, args, world, tune) if args.seeds > 0 else None
 
     bytes_step = alg_bytes(M, N, Z, vb, xb, xb)
     gbs = bytes_step / (ms_perm * 1e-3) / 1e9  # one replica; the job's value is job_rate over all ranks
@@ -831,7 +895,9 @@ def main():
         "permuted_over_plain": round(ms_plain / ms_perm, 4),
         "kernel_variant": {"permuted_items_per_lane": hP.items_per_lane(), "plain_items_per_lane": hN.items_per_lane(),
                            "permuted_xslice": hP.xslice(), "plain_xslice": hN.xslice()},
-        "flushed_l2_launch_ms": {"permuted": fl_perm, "plain": fl_plain},
+        "flushed_l2_launch_ms": {"permuted": fl_perm, "plain": fl_plain, "what": "median of 200 launches, "
+                                 "a 256 MB write before each"},
+        "seeds": seeds,
         "full_path": {"value": round(bytes_step / (ms_full * 1e-3) / 1e9, 3), "unit": "GB/s",
                       "ms_per_step": ms_full, "what": "y = A x in the original space: x gather + SpMV with fused "
                                                       "y scatter (algorithmic bytes of the product only)"},
@@ -856,6 +922,7 @@ def main():
         got = yP.cpu().double().numpy()
         out["cpu_baseline"] = {"value": round(bytes_step / t_cpu / 1e9, 4), "unit": "GB/s", "cores": 1,
                                "kind": "oracle", "sample": f"full permuted matrix, {reps} products, FP64 oracle",
+                               "host": host_info(),
                                "rel_l2_gpu_vs_oracle": float(np.linalg.norm(got - y_cpu) /
                                                              max(np.linalg.norm(y_cpu), 1e-300))}
     if rank == 0:
