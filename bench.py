@@ -427,7 +427,7 @@ def run_batched(args):
         if not (args.profile or args.no_tune):
             maxe.maxe_batch_tune(h, k)
         hs.append(h)
-        kp = (k + 3) // 4 * 4  # leading dimension padded to 4 columns: 16-byte rows
+        kp = 1 if k == 1 else (k + 3) // 4 * 4  # 16-byte rows for k > 1; unit strides for SpMV
         Xb = torch.zeros(A.cols, kp, device="cuda")
         Xb[:, :k] = W.matrix_rhs(m, A.cols, k, "f32", "cuda")
         Xs.append(Xb[:, :k])
@@ -535,7 +535,7 @@ def run_serving(args):
             maxe.maxe_spmv(h, u, w, permuted=True)
             maxe.maxe_vec_dot_gather(srv.Q[r.mat], u, w, scratch, lam)
         else:
-            kp = (r.k + 3) // 4 * 4  # same padded layout as the server's buffers
+            kp = 1 if r.k == 1 else (r.k + 3) // 4 * 4  # same layout as the server's buffers
             X = torch.rand(A.cols, kp, device="cuda") * 2 - 1
             Y = torch.empty(A.rows, kp, device="cuda")
             maxe.maxe_spmm(h, X[:, :r.k], Y[:, :r.k], permuted=True)

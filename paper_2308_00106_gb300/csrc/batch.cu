@@ -58,7 +58,7 @@ constexpr int kClasses = 3;
 
 template <typename VT, int CLASS>
 struct BatchClass {
-  static constexpr int kMinBlocks = CLASS == 0 ? (sizeof(typename Acc<VT>::T) == 8 ? 3 : 4) : 2;
+  static constexpr int kMinBlocks = CLASS == 0 ? 3 : 2;  // class 0 at 4 blocks spills (64 registers)
   static constexpr size_t warp_smem() {
     size_t m = 0;
     if (CLASS == 0) m = sizeof(WarpSmem<VT, 1, 8>);

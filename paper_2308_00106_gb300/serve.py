@@ -16,7 +16,9 @@ in the library's batched persistent kernel (maxe_batch_run) and every vector
 step in its kernels (maxe_vec_norm_gather / maxe_vec_dot_gather).
 
 Continuous batching: requests are admitted as soon as their buffers fit under
-the device-memory cap; each batch step takes one unit of work (a product) from
+the device-memory cap (and while the admitted work waiting for a step is under
+about two steps per stream, so admitting interleaves with launching); each
+batch step takes one unit of work (a product) from
 admitted requests that are not already on the GPU, oldest first, up to a byte
 budget of work per step, so requests join and leave between steps and a power
 iteration advances one product per step.  Two CUDA streams, each with its own
@@ -114,11 +116,16 @@ class Server:
         self.batches = [maxe.Batch(batch_capacity, stream=s) for s in self.streams]
         self.capacity = batch_capacity
         self.step_bytes = step_bytes  # work per batch step, so that the streams alternate and overlap
+        # admitted work waiting for a step is kept to about two steps per stream, so
+        # that admitting (host allocations, input initialisation) interleaves with
+        # launching instead of preceding it
+        self.backlog_bytes = 2 * streams * step_bytes
+        self.gen = torch.Generator(device="cuda")  # re-seeded per request
 
     # ---------------------------------------------------------------- helpers
     def request_bytes(self, r: Request) -> int:
         A = self.mats[r.mat]
-        b = (A.cols + A.rows) * ((r.k + 3) // 4 * 4) * 4
+        b = (A.cols + A.rows) * (1 if r.k == 1 else (r.k + 3) // 4 * 4) * 4
         if r.kind == "power":
             b += (A.cols + A.rows) * 4 + 1024 * 8
         return b
@@ -131,7 +138,7 @@ class Server:
     def _admit(self, r: Request, stream):
         A = self.mats[r.mat]
         with torch.cuda.stream(stream):
-            g = torch.Generator(device="cuda")
+            g = self.gen
             g.manual_seed(r.seed)
             if r.kind == "power":
                 u = torch.rand(A.cols, generator=g, device="cuda") * 2 - 1
@@ -139,9 +146,14 @@ class Server:
                           "scratch": torch.empty(1024, dtype=torch.float64, device="cuda"),
                           "lam": torch.empty(1, dtype=torch.float64, device="cuda"), "u0": u.clone()}
             else:
-                kp = (r.k + 3) // 4 * 4  # 16-byte rows: the kernel gathers 4 columns per load
-                X = torch.zeros(A.cols, kp, device="cuda")
-                X[:, :r.k] = torch.rand(A.cols, r.k, generator=g, device="cuda") * 2 - 1
+                # 16-byte rows for k > 1 (the kernel gathers 4 columns per load); unit
+                # strides for k = 1, which the batched kernel runs in its SpMV class
+                kp = 1 if r.k == 1 else (r.k + 3) // 4 * 4
+                if kp == r.k:
+                    X = torch.rand(A.cols, r.k, generator=g, device="cuda").mul_(2).sub_(1)
+                else:
+                    X = torch.zeros(A.cols, kp, device="cuda")
+                    X[:, :r.k] = torch.rand(A.cols, r.k, generator=g, device="cuda") * 2 - 1
                 r.bufs = {"X": X[:, :r.k], "Y": torch.empty(A.rows, kp, device="cuda")[:, :r.k]}
 
     def _launch(self, si: int, reqs):
@@ -191,6 +203,7 @@ class Server:
         ready = collections.deque()
         inflight = {}  # stream index -> (event, requests)
         mem_used = 0
+        ready_work = 0  # unit bytes of admitted requests waiting for a step
         nxt = done = 0
         bytes_done = 0
         steps = 0
@@ -205,13 +218,15 @@ class Server:
             while nxt < n and trace[nxt].arrival <= now:
                 waiting.append(trace[nxt])
                 nxt += 1
-            while waiting and mem_used + self.request_bytes(waiting[0]) <= self.mem_cap - self.resident_bytes:
+            while (waiting and mem_used + self.request_bytes(waiting[0]) <= self.mem_cap - self.resident_bytes
+                   and ready_work < self.backlog_bytes):
                 r = waiting.popleft()
                 mem_used += self.request_bytes(r)
                 peak_mem = max(peak_mem, mem_used)
                 self._admit(r, self.adm_stream)
                 r.t_admit = time.perf_counter() - t0
                 ready.append(r)
+                ready_work += self.unit_bytes(r)
                 progressed = True
             for si in list(inflight):
                 ev, reqs = inflight[si]
@@ -229,6 +244,7 @@ class Server:
                         done += 1
                     else:
                         ready.append(r)
+                        ready_work += self.unit_bytes(r)
                 progressed = True
             for si in range(len(self.streams)):
                 if si in inflight or not ready:
@@ -238,6 +254,7 @@ class Server:
                     r = ready.popleft()
                     take.append(r)
                     work += self.unit_bytes(r)
+                ready_work -= work
                 # the first step of a freshly admitted request must see its initialised buffers
                 self.streams[si].wait_stream(self.adm_stream)
                 inflight[si] = (self._launch(si, take), take)
