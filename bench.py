@@ -624,7 +624,7 @@ def run_laplacian_table(args):
                                  "build_s": round(t_build, 4)})
             h.close()
     clk = clocks.stop()
-    out = {"metric": "SpMV/SpMM GB/s and frac of HBM roofline, 5-point Laplacian n=4096 (config 3)",
+    out = {"metric": "SpMV/SpMM GB/s and frac of HBM roofline, 5-point Laplacian on a 4096 x 4096 grid",
            "unit": "GB/s", "peak": hbm, "peak_source": src, "rows": M, "nnz": base.nnz,
            "timing": f"{K} steps, CUDA graph of 5, CUDA events; inputs larger than L2 (matrix >= 0.5 GB)",
            "table": rows_out, "clocks": clk}

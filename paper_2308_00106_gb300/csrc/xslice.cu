@@ -9,7 +9,7 @@
 //   - a producer warp loads the slices of x the tile touches, in order, into a
 //     shared-memory ring of three (FP64: two) slices with 1-D bulk copies (TMA;
 //     64 KB, L2 evict-last so x stays in L2 for the other SMs);
-//   - 16 consumer warps each own a contiguous range of the tile's rows
+//   - 15 consumer warps each own a contiguous range of the tile's rows
 //     (nnz-balanced) and a row accumulator per row in shared memory; for every
 //     slice a warp streams its own entries of that slice -- (row, column in
 //     slice) packed in 32 bits, and the value -- with 16-byte loads, gathers x

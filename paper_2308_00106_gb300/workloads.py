@@ -148,7 +148,7 @@ def from_lengths(seed: int, lengths, cols: int, dtype: str = "f32", device="cpu"
 
 def blockdiag(seed: int = 2308, n: int = 4096, blocks: int = 16, fill: float = 0.02, offblock: int = 2000,
               dtype: str = "f64", device="cpu") -> CSR:
-    """Config: 16 dense-ish diagonal blocks at 2% fill plus 2000 uniform off-block entries."""
+    """4096 x 4096: 16 dense-ish diagonal blocks at 2% fill plus 2000 uniform off-block entries."""
     g = _gen(seed, device)
     bs = n // blocks
     mask = torch.rand((blocks, bs, bs), generator=g, device=device) < fill
@@ -185,7 +185,7 @@ def zipf_lengths(n: int, s: float, cap: int, g, device) -> torch.Tensor:
 
 def powerlaw(seed: int = 2308, n: int = 1 << 20, zipf_s: float = 1.5, cap: int = 1000, sigma: float = 2000.0,
              dtype: str = "f32", device="cpu", length_scale: float = 1.0) -> CSR:
-    """Config: power-law rows clustered near the diagonal (Gaussian columns)."""
+    """Power-law row lengths, columns clustered near the diagonal (Gaussian)."""
     g = _gen(seed, device)
     lengths = zipf_lengths(n, zipf_s, cap, g, device)
     if length_scale != 1.0:
@@ -202,7 +202,7 @@ def powerlaw(seed: int = 2308, n: int = 1 << 20, zipf_s: float = 1.5, cap: int =
 
 
 def laplacian5(n: int = 4096, dtype: str = "f64", device="cpu") -> CSR:
-    """Config: 5-point Laplacian on an n x n grid, natural (row-major) order."""
+    """5-point Laplacian on an n x n grid, natural (row-major) order."""
     M = n * n
     idx = torch.arange(M, device=device, dtype=torch.int64)
     p, q = idx // n, idx % n
@@ -228,7 +228,7 @@ def poisson_uniform(seed: int, rows: int, lam: float, dtype: str = "f32", device
 
 def batched_set(seed: int = 2308, count: int = 256, rows_lo: int = 1000, rows_hi: int = 200_000,
                 lam_lo: float = 8.0, lam_hi: float = 64.0, kmax: int = 16, dtype: str = "f32", device="cpu"):
-    """Config: uneven matrices (rows log-uniform, Poisson row lengths) each with 1..kmax RHS."""
+    """Uneven matrices (rows log-uniform, Poisson row lengths), each with 1..kmax right-hand sides."""
     rng = np.random.default_rng(seed)
     rows = np.exp(rng.uniform(math.log(rows_lo), math.log(rows_hi), count)).round().astype(np.int64)
     lams = rng.uniform(lam_lo, lam_hi, count)
@@ -239,7 +239,7 @@ def batched_set(seed: int = 2308, count: int = 256, rows_lo: int = 1000, rows_hi
 
 def serving_set(seed: int = 2308, count: int = 64, rows_lo: int = 10_000, rows_hi: int = 4_000_000,
                 lam_lo: float = 5.0, lam_hi: float = 50.0, device="cpu"):
-    """Config: resident matrices of the serving loop, half FP32 and half BF16 values."""
+    """Resident matrices of the serving loop, half FP32 and half BF16 values."""
     rng = np.random.default_rng(seed + 1)
     rows = np.exp(rng.uniform(math.log(rows_lo), math.log(rows_hi), count)).round().astype(np.int64)
     lams = rng.uniform(lam_lo, lam_hi, count)
