@@ -892,6 +892,8 @@ def main():
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "plain": {"value": round(gbs_plain * world, 3), "unit": "GB/s", "ms_per_step": ms_plain,
                   "frac": round(gbs_plain / hbm, 4)},
+        "gflops": {"permuted": round(2 * Z * world / (ms_perm * 1e-3) / 1e9, 2),
+                   "plain": round(2 * Z * world / (ms_plain * 1e-3) / 1e9, 2), "what": "2 nnz / time"},
         "permuted_over_plain": round(ms_plain / ms_perm, 4),
         "kernel_variant": {"permuted_items_per_lane": hP.items_per_lane(), "plain_items_per_lane": hN.items_per_lane(),
                            "permuted_xslice": hP.xslice(), "plain_xslice": hN.xslice()},
