@@ -20,7 +20,8 @@
 //     (head, tail) and a second kernel adds them up, in chunk order, for every
 //     row that crosses a chunk boundary.
 //   - Rows with no entries are written as zeros by the lane holding the next
-//     row's first entry (and the last entry zeroes the rows after it).
+//     row's first entry (and the last entry zeroes the rows after it); runs of
+//     more than 32 empty rows by the whole warp.
 #include <algorithm>
 
 #include "handle.cuh"
@@ -163,11 +164,22 @@ __global__ void __launch_bounds__(32 * kWarps) coo_spmv_kernel(const int32_t* __
   // empty rows before each row start (and after the last entry)
   int32_t prev = __shfl_up_sync(0xffffffffu, r[kItems - 1], 1);
   if (lane == 0) prev = cb > 0 ? row[cb - 1] : -1;
+  // a gap of up to 32 rows is written by its lane; a longer one by the whole warp
 #pragma unroll
-  for (int j = 0; j < kItems; ++j) {
-    const int32_t pr = j == 0 ? prev : r[j - 1];
-    if (e0 + j < Z && r[j] != pr) zero_rows(y, yperm, pr + 1, r[j]);
-    if (e0 + j == Z - 1) zero_rows(y, yperm, r[j] + 1, M);
+  for (int j = 0; j <= kItems; ++j) {
+    int32_t ga = 0, gb = 0;
+    if (j < kItems) {
+      const int32_t pr = j == 0 ? prev : r[j - 1];
+      if (e0 + j < Z && r[j] != pr) ga = pr + 1, gb = r[j];
+    } else if (e0 <= Z - 1 && Z - 1 < e0 + kItems) {  // the rows after the last entry
+      ga = row[Z - 1] + 1, gb = M;
+    }
+    if (gb - ga <= 32) zero_rows(y, yperm, ga, gb);
+    for (unsigned m = __ballot_sync(0xffffffffu, gb - ga > 32); m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const int32_t a = __shfl_sync(0xffffffffu, ga, src), b = __shfl_sync(0xffffffffu, gb, src);
+      for (int32_t q = a + lane; q < b; q += 32) put(y, yperm, q, VT(0));
+    }
   }
 
   // lane-local segments: first (head), middle (whole rows), last (tail)

@@ -76,6 +76,24 @@ def test_coo_single_long_row_spans_many_chunks():
     assert rel_l2(y.cpu().numpy(), oracle.spmv(A.rows, rp, co, va, code("f64"), x.cpu().numpy())) <= TOL["f64"]
 
 
+def test_coo_long_runs_of_empty_rows():
+    """Runs of empty rows longer than a warp (zeroed by the whole warp), at the
+    start, in the middle and after the last entry."""
+    lengths = np.zeros(300000, dtype=np.int64)
+    lengths[[70000, 70001, 150000, 200000]] = [5, 300, 2, 40]
+    A = W.from_lengths(4, lengths, 1000, "f32")
+    rperm = maxe.maxe_build_permutation(3, A.rows, 0)
+    h = maxe.from_csr(A.to("cuda"), rperm, None, coo=True)
+    x = W.vector(2, A.cols, "f32", "cuda")
+    for permuted in (False, True):
+        y = torch.full((A.rows,), float("nan"), device="cuda")
+        maxe.maxe_coo_spmv(h, x, y, permuted=permuted)
+        assert not torch.isnan(y).any()
+    rp, co, va = A.numpy()
+    y = maxe.maxe_coo_spmv(h, x)
+    assert rel_l2(y.cpu().numpy(), oracle.spmv(A.rows, rp, co, va, code("f32"), x.cpu().numpy())) <= TOL["f32"]
+
+
 def test_coo_requires_the_flag():
     A = W.laplacian5(8, "f32").to("cuda")
     h = maxe.from_csr(A)
