@@ -332,7 +332,11 @@ def run_reference(args):
     import oracle
     from paper_2308_00106_gb300 import workloads as W
     oracle.build()
-    A, dtype, desc = make_workload(args.workload, args.seed, "cpu")
+    # the same matrix as the GPU arm: generated by the same torch stream (on the
+    # GPU when there is one; input generation only, outside the timed region)
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A, dtype, desc = make_workload(args.workload, args.seed, gen_dev)
+    A = A.to("cpu")
     rp, co, va = A.numpy()
     M, N, Z = A.rows, A.cols, A.nnz
     rperm = oracle.build_permutation(args.seed, M, 0)
@@ -399,7 +403,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "variant": "permuted R-C, vectors in permuted space"},
+        "config": {"workload": desc, "variant": "permuted R-C, vectors in permuted space", "nnz": Z,
+                   "inputs": f"generated with torch on {gen_dev} (the GPU arm's stream when on cuda)"},
         "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "host": host_info()},
         "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
