@@ -166,8 +166,14 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   maxe_status s = permute_csr_run(A, rperm, cperm, flags, h, st);
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
   if (s == MAXE_OK && (flags & MAXE_COO)) s = coo_build(h, st);
-  if (s == MAXE_OK && (flags & (MAXE_XSLICE | MAXE_AUTOTUNE)) && !h->equal_rows)
+  if (s == MAXE_OK && (flags & (MAXE_XSLICE | MAXE_AUTOTUNE)) && !h->equal_rows) {
     s = xslice_build(h, st, (flags & MAXE_XSLICE) != 0);
+    // only the autotuner asked for it: without the memory, the handle goes without it
+    if (s == MAXE_ERR_OOM && !(flags & MAXE_XSLICE)) {
+      xslice_release(h);
+      s = MAXE_OK;
+    }
+  }
   if (s == MAXE_OK) s = batch_plan_default(h, st);
   if (s == MAXE_OK && (flags & MAXE_ITEMS16)) h->spmv_items16 = 1;
   if (s == MAXE_OK && (flags & MAXE_SPMM_LANES)) h->spmm_lc = 1;
