@@ -36,10 +36,11 @@ struct maxe_handle {
   int bit16 = 0;                           // batch plan: 16 entries per lane for k = 1
   int blc = 0;                             // batch plan: SpMM with columns across lanes
   // x-sliced SpMV form (MAXE_XSLICE): entries grouped by (warp range, column slice)
-  uint32_t* xs_idx = nullptr;              // (tile-local row << slice bits) | column in slice
+  uint32_t* xs_idx = nullptr;              // (accumulator << 15) | column in slice, step-major cells
   void* xs_val = nullptr;
-  int32_t* xs_seg_start = nullptr;         // [G * nS], xs_seg_len follows in the same block
+  int32_t* xs_seg_start = nullptr;         // [G * nS], xs_seg_len and xs_seg_cut follow in the same block
   int32_t* xs_seg_len = nullptr;
+  uint32_t* xs_seg_cut = nullptr;          // [G * nS] lane-boundary cuts of each cell
   int32_t* xs_tile_row = nullptr;          // [ntiles + 1]
   int32_t* xs_warp_row = nullptr;          // [G + 1]
   int32_t* xs_tl_off = nullptr;            // [ntiles + 1], xs_tl_slice follows in the same block

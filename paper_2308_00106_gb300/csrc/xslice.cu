@@ -10,21 +10,27 @@
 //     shared-memory ring of three (FP64: two) slices with 1-D bulk copies (TMA;
 //     64 KB, L2 evict-last so x stays in L2 for the other SMs);
 //   - 15 consumer warps each own a contiguous range of the tile's rows
-//     (nnz-balanced) and a row accumulator per row in shared memory; for every
-//     slice a warp streams its own entries of that slice -- (row, column in
-//     slice) packed in 32 bits, and the value -- with 16-byte loads, gathers x
-//     from shared memory, sums rows with a segmented shuffle scan and adds each
-//     row's partial sum to its accumulator;
+//     (nnz-balanced) and a row accumulator per row in shared memory; the
+//     entries of one warp range and one slice (a cell, in row order) are cut
+//     into 32 contiguous runs of equal length, one per lane, and stored step by
+//     step (entry j of every lane's run side by side), so a warp reads a cell
+//     with one coalesced 128-byte load per step and no lane idles;
+//   - every entry adds a * x[col] to its row's accumulator.  A row that a lane
+//     boundary cuts is split: the entries before the cut go to the lane's own
+//     scratch accumulator, the ones after it to the row, and after the cell the
+//     scratch sums are added to the row by the lane that holds the row's last
+//     run (a shuffle, or a segmented scan when a row crosses a whole lane);
 //   - at the end of the tile every warp writes its rows of y (through rperm
 //     when y is wanted in the original space).
 //
-// Each accumulator is touched by one warp only, in slice order and then entry
-// order, so the result is deterministic.  The format is built once from the
-// handle's CSR (a stable sort by (warp range, slice)); it pays when the rows of
-// a tile hit most x sectors of the slices they touch, i.e. for matrices with
-// many nonzeros per column of a tile (the 1M-row power-law matrix permuted),
-// and unless asked for explicitly it is skipped when the estimated x traffic
-// exceeds four times the matrix.
+// Within a cell every accumulator has one writer lane, across cells the order
+// is slice order, and the scratch sums are combined in lane order, so the
+// result is deterministic.  The format is built once from the handle's CSR (a
+// stable sort by (warp range, slice)); it pays when the rows of a tile hit most
+// x sectors of the slices they touch, i.e. for matrices with many nonzeros per
+// column of a tile (the 1M-row power-law matrix permuted), and unless asked
+// for explicitly it is skipped when the estimated x traffic exceeds four times
+// the matrix.
 #include <algorithm>
 #include <vector>
 
@@ -35,10 +41,11 @@ namespace {
 
 constexpr int kXsWarps = 15;  // consumer warps per CTA; with the producer, 4 warps per SM sub-partition
 constexpr int kXsThreads = 32 * (kXsWarps + 1);
-constexpr int kXsItems = 8;  // entries per lane per chunk
-constexpr int kXsChunk = 32 * kXsItems;
-constexpr int kXsAlign = 8;    // segment starts padded to 8 entries: 16-byte loads of idx and values
-constexpr int kXsSlack = 256;  // zeroed entries after the last segment (whole-vector loads at the end)
+constexpr int kXsSteps = 8;     // steps of a cell per register group
+constexpr int kXsAlign = 32;    // cell starts padded to 32 entries: each step is one aligned run of 32
+constexpr int kXsSlack = 256;   // zeroed entries after the last cell
+constexpr int kXsColBits = 15;  // idx = (accumulator << 15) | column in slice; column S is a zero
+constexpr uint32_t kXsColMask = (1u << kXsColBits) - 1u;
 
 template <typename VT>
 struct XsCfg;
@@ -46,28 +53,42 @@ template <>
 struct XsCfg<float> {
   static constexpr int kSliceBits = 14;  // 16384 columns, 64 KB
   static constexpr int kBuffers = 3;     // slices in the ring: two loads in flight while one is read
-  static constexpr int kRows = 8192;     // rows per tile, 32 KB of accumulators
-  static constexpr int kDepth = 2;       // chunks per warp in registers (one summed, one in flight)
+  static constexpr int kRows = 8192;     // rows per tile
+  static constexpr int kDepth = 2;       // register groups per warp (one summed, one in flight)
 };
 template <>
 struct XsCfg<double> {
   static constexpr int kSliceBits = 13;  // 8192 columns, 64 KB
   static constexpr int kBuffers = 2;
-  static constexpr int kRows = 8192;     // 64 KB
+  static constexpr int kRows = 8192;
   static constexpr int kDepth = 2;
 };
 
+// One slot of the ring: the slice and 16 bytes after it, the first element of
+// which stays zero (the column of the entries a lane pads its run with).
+template <typename VT>
+constexpr int xs_slot_elems() {
+  return (1 << XsCfg<VT>::kSliceBits) + 16 / static_cast<int>(sizeof(VT));
+}
+
+// Accumulators: kRows rows of the tile, then 32 scratch sums per consumer warp.
+template <typename VT>
+constexpr int xs_acc_elems() {
+  return XsCfg<VT>::kRows + 32 * kXsWarps;
+}
+
 template <typename VT>
 constexpr size_t xs_smem_bytes() {
-  return sizeof(VT) * (XsCfg<VT>::kBuffers * (size_t(1) << XsCfg<VT>::kSliceBits) + XsCfg<VT>::kRows) +
+  return sizeof(VT) * (XsCfg<VT>::kBuffers * static_cast<size_t>(xs_slot_elems<VT>()) + xs_acc_elems<VT>()) +
          16 * XsCfg<VT>::kBuffers + 16;
 }
 
 struct XsParams {
-  const uint32_t* idx;        // (tile-local row << kSliceBits) | column in slice
+  const uint32_t* idx;        // (accumulator << 15) | column in slice, cell by cell, step-major
   const void* val;            // values, aligned with idx
-  const int32_t* seg_start;   // [G * nS] first entry of (warp range, slice)
+  const int32_t* seg_start;   // [G * nS] first slot of (warp range, slice)
   const int32_t* seg_len;     // [G * nS] entries of (warp range, slice)
+  const uint32_t* seg_cut;    // [G * nS] bit l: the last row of lane l's run continues in lane l + 1
   const int32_t* tile_row;    // [ntiles + 1]
   const int32_t* warp_row;    // [G + 1] first (global) row of each warp range
   const int32_t* tl_off;      // [ntiles + 1] into tl_slice
@@ -85,141 +106,52 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   return pol;
 }
 
-template <typename VT>
-struct XsVals;
+template <typename ValT>
+struct XsVal;
 template <>
-struct XsVals<double> {  // FP64 values
+struct XsVal<double> {  // FP64 values
   using AT = double;
-  static __device__ __forceinline__ void load(const void* v, int64_t e, double (&a)[kXsItems]) {
-    const double2* p = reinterpret_cast<const double2*>(static_cast<const double*>(v) + e);
-#pragma unroll
-    for (int q = 0; q < kXsItems / 2; ++q) {
-      const double2 t = __ldcs(p + q);
-      a[2 * q] = t.x;
-      a[2 * q + 1] = t.y;
-    }
+  static __device__ __forceinline__ double ld(const void* v, int64_t e) {
+    return __ldcs(static_cast<const double*>(v) + e);
   }
 };
 template <>
-struct XsVals<float> {  // FP32 values
+struct XsVal<float> {  // FP32 values
   using AT = float;
-  static __device__ __forceinline__ void load(const void* v, int64_t e, float (&a)[kXsItems]) {
-    const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(v) + e);
-#pragma unroll
-    for (int q = 0; q < kXsItems / 4; ++q) {
-      const float4 t = __ldcs(p + q);
-      a[4 * q] = t.x;
-      a[4 * q + 1] = t.y;
-      a[4 * q + 2] = t.z;
-      a[4 * q + 3] = t.w;
-    }
+  static __device__ __forceinline__ float ld(const void* v, int64_t e) {
+    return __ldcs(static_cast<const float*>(v) + e);
   }
 };
 template <>
-struct XsVals<uint16_t> {  // BF16 values, FP32 arithmetic
+struct XsVal<uint16_t> {  // BF16 values, FP32 arithmetic
   using AT = float;
-  static __device__ __forceinline__ void load(const void* v, int64_t e, float (&a)[kXsItems]) {
-    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(v) + e);
-#pragma unroll
-    for (int h = 0; h < kXsItems / 8; ++h) {
-      const uint4 t = __ldcs(p + h);
-      const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[8 * h + 2 * q] = __uint_as_float(w[q] << 16);
-        a[8 * h + 2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
-      }
-    }
+  static __device__ __forceinline__ float ld(const void* v, int64_t e) {
+    return __uint_as_float(static_cast<uint32_t>(__ldcs(static_cast<const unsigned short*>(v) + e)) << 16);
   }
 };
 
-// One chunk of a warp's entries in registers: 8 consecutive entries per lane.
-template <typename VT>
-struct XsChunk {
-  uint32_t id[kXsItems];
-  VT a[kXsItems];
-  int nval;  // valid entries of this lane (<= 0: none)
+// A group of up to kXsSteps consecutive steps of a lane's run, in registers.
+template <typename AT>
+struct XsGroup {
+  uint32_t id[kXsSteps];
+  AT a[kXsSteps];
 };
 
-template <typename VT, typename ValT>
-__device__ __forceinline__ void xs_load(const XsParams& p, int32_t st, int32_t len, int32_t c, int lane,
-                                        XsChunk<VT>& k) {
-  const int32_t off = c + lane * kXsItems;
-  k.nval = min(kXsItems, len - off);
-  if (k.nval > 0) {
-    const uint4* ip = reinterpret_cast<const uint4*>(p.idx + st + off);
-#pragma unroll
-    for (int q = 0; q < kXsItems / 4; ++q) {
-      const uint4 u = __ldcs(ip + q);
-      k.id[4 * q] = u.x, k.id[4 * q + 1] = u.y, k.id[4 * q + 2] = u.z, k.id[4 * q + 3] = u.w;
-    }
-    XsVals<ValT>::load(p.val, static_cast<int64_t>(st) + off, k.a);
-  }
-}
-
-// acc[row] += the chunk's entries of each row, x gathered from the slice in xs.
-template <typename VT>
-__device__ __forceinline__ void xs_compute(const XsChunk<VT>& k, const VT* __restrict__ xs, VT* __restrict__ acc,
-                                           int lane) {
-  constexpr int SB = XsCfg<VT>::kSliceBits;
-  constexpr uint32_t kMask = (1u << SB) - 1u;
-  constexpr int32_t kNone = 0x7fffffff;  // sentinel row of entries past the segment
-  int32_t rw[kXsItems];
-  VT pr[kXsItems];
-#pragma unroll
-  for (int j = 0; j < kXsItems; ++j) {
-    const bool v = j < k.nval;
-    rw[j] = v ? static_cast<int32_t>(k.id[j] >> SB) : kNone;
-    pr[j] = v ? k.a[j] * xs[k.id[j] & kMask] : VT(0);
-  }
-  // lane-local segments: a segment bounded inside the lane is the whole of the
-  // row's entries in this chunk and goes straight to its accumulator
-  VT run = VT(0), hd = VT(0);
-  bool single = true;
-#pragma unroll
-  for (int j = 0; j < kXsItems; ++j) {
-    run += pr[j];
-    if (j + 1 < kXsItems && rw[j + 1] != rw[j]) {
-      if (single)
-        hd = run;
-      else
-        acc[rw[j]] += run;  // rw[j] < kNone: a sentinel is never followed by another row
-      single = false;
-      run = VT(0);
-    }
-  }
-  const int32_t F = rw[0], R = rw[kXsItems - 1];
-  const int32_t Rprev = __shfl_up_sync(0xffffffffu, R, 1);
-  // segmented inclusive scan of the lanes' last segments
-  int flag = (lane == 0 || !single || Rprev != R) ? 1 : 0;
-  VT S = run;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const VT s_up = __shfl_up_sync(0xffffffffu, S, d);
-    const int f_up = __shfl_up_sync(0xffffffffu, flag, d);
-    if (lane >= d && !flag) S += s_up;
-    if (lane >= d) flag |= f_up;
-  }
-  const VT Sprev = __shfl_up_sync(0xffffffffu, S, 1);
-  const int32_t Fnext = __shfl_down_sync(0xffffffffu, F, 1);
-  if (!single) acc[F] += hd + ((lane > 0 && Rprev == F) ? Sprev : VT(0));
-  if (R != kNone && (lane == 31 || Fnext != R)) acc[R] += S;
-  __syncwarp();
-}
-
-// Position of a chunk in a warp's stream over the tile's slices: slice index i
-// (into tl_slice), the segment [st, st + len) and the chunk offset c; i = -1
-// past the end.  The segments of 32 slices at a time sit in the lanes
-// (lane l: slice index base + l), so finding the next slice with entries is a
-// ballot.
+// Position of a group in a warp's stream over the tile's slices: slice index i
+// (into tl_slice), the cell [st, st + n) with its cut mask, and the first step
+// s0 of the group; i = -1 past the end.  The cells of 32 slices at a time sit
+// in the lanes (lane l: slice index base + l), so finding the next slice with
+// entries is a ballot.
 struct XsPos {
   int i;
-  int32_t st, len, c;
+  int32_t st, n, s0;
+  uint32_t cut;
 };
 
 struct XsWindow {
   int base;  // slice index held by lane 0
-  int32_t st, len;
+  int32_t st, n;
+  uint32_t cut;
 };
 
 __device__ __forceinline__ void xs_window_load(const XsParams& p, int64_t g, int i_end, int base, int lane,
@@ -229,51 +161,125 @@ __device__ __forceinline__ void xs_window_load(const XsParams& p, int64_t g, int
   if (i < i_end) {
     const int64_t key = g * p.nS + p.tl_slice[i];
     w.st = p.seg_start[key];
-    w.len = p.seg_len[key];
+    w.n = p.seg_len[key];
+    w.cut = p.seg_cut[key];
   } else {
     w.st = 0;
-    w.len = 0;
+    w.n = 0;
+    w.cut = 0;
   }
 }
 
-// The first chunk in a slice index > i (or >= i when `from` is set) with entries.
+// The first group of the first slice index > i with entries of this warp.
 __device__ __forceinline__ XsPos xs_next_slice(const XsParams& p, int64_t g, int i, int i_end, int lane,
                                                XsWindow& w) {
   while (true) {
     const int li = w.base + lane;
-    const unsigned m = __ballot_sync(0xffffffffu, li > i && li < i_end && w.len > 0);
+    const unsigned m = __ballot_sync(0xffffffffu, li > i && li < i_end && w.n > 0);
     if (m) {
       const int src = __ffs(m) - 1;
       XsPos q;
       q.i = w.base + src;
       q.st = __shfl_sync(0xffffffffu, w.st, src);
-      q.len = __shfl_sync(0xffffffffu, w.len, src);
-      q.c = 0;
+      q.n = __shfl_sync(0xffffffffu, w.n, src);
+      q.cut = __shfl_sync(0xffffffffu, w.cut, src);
+      q.s0 = 0;
       return q;
     }
-    if (w.base + 32 >= i_end) return XsPos{-1, 0, 0, 0};
+    if (w.base + 32 >= i_end) return XsPos{-1, 0, 0, 0, 0u};
     xs_window_load(p, g, i_end, w.base + 32, lane, w);
   }
 }
 
+__device__ __forceinline__ int32_t xs_steps(int32_t n) { return (n + 31) >> 5; }
+
 __device__ __forceinline__ XsPos xs_next(const XsParams& p, int64_t g, const XsPos& q, int i_end, int lane,
                                          XsWindow& w) {
   if (q.i < 0) return q;
-  if (q.c + kXsChunk < q.len) return XsPos{q.i, q.st, q.len, q.c + kXsChunk};
+  if (q.s0 + kXsSteps < xs_steps(q.n)) return XsPos{q.i, q.st, q.n, q.s0 + kXsSteps, q.cut};
   return xs_next_slice(p, g, q.i, i_end, lane, w);
+}
+
+// Load the group's steps of this lane's run; steps past the run hold `pad`
+// (the lane's scratch accumulator, the zero column) and value 0.
+template <typename ValT>
+__device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int lane, uint32_t pad,
+                                        XsGroup<typename XsVal<ValT>::AT>& k) {
+  using AT = typename XsVal<ValT>::AT;
+  const int32_t L = xs_steps(q.n);
+  const int32_t len = L - (lane >= q.n - 32 * (L - 1) ? 1 : 0);  // entries of this lane's run
+  const int64_t base = static_cast<int64_t>(q.st) + static_cast<int64_t>(q.s0) * 32 + lane;
+#pragma unroll
+  for (int j = 0; j < kXsSteps; ++j) {
+    const bool v = q.s0 + j < len;
+    k.id[j] = v ? __ldcs(p.idx + base + 32 * j) : pad;
+    k.a[j] = v ? XsVal<ValT>::ld(p.val, base + 32 * j) : AT(0);
+  }
+}
+
+// acc[slot] += a * x[column] for the group's first ns steps.
+template <typename VT, typename AT>
+__device__ __forceinline__ void xs_compute(const XsGroup<AT>& k, int ns, const VT* __restrict__ xs,
+                                           VT* __restrict__ acc) {
+#pragma unroll
+  for (int j = 0; j < kXsSteps; ++j) {
+    if (j < ns) {
+      const uint32_t u = k.id[j];
+      const VT xv = xs[u & kXsColMask];
+      VT* ap = acc + (u >> kXsColBits);
+      *ap = fma(static_cast<VT>(k.a[j]), xv, *ap);
+    }
+  }
+}
+
+// After a cell: add the scratch sums of the rows cut by lane boundaries to the
+// rows.  cut bit l: lane l's last row continues in lane l + 1 (its entries of
+// that row went to scratch[l]).  f0: the accumulator of the lane's first
+// entry -- a row, or the lane's scratch when the lane's first row continues
+// (then the lane holds that row only).  The lane whose first row came from the
+// previous lane and ends in it adds the chain's scratch sums, in lane order.
+template <typename VT>
+__device__ __forceinline__ void xs_combine(uint32_t cut, uint32_t f0, VT* __restrict__ acc,
+                                           VT* __restrict__ scratch, int lane) {
+  constexpr uint32_t kRows = XsCfg<VT>::kRows;
+  const bool out = (cut >> lane) & 1u;
+  const bool in = lane > 0 && ((cut >> (lane - 1)) & 1u);
+  VT v = VT(0);
+  if (out) {
+    v = scratch[lane];
+    scratch[lane] = VT(0);
+  }
+  const bool through = in && f0 >= kRows;  // one row, continuing on both sides
+  if (__ballot_sync(0xffffffffu, through)) {
+    // segmented inclusive scan: a lane the row runs through adds the sum so far
+    int head = through ? 0 : 1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const VT t = __shfl_up_sync(0xffffffffu, v, d);
+      const int th = __shfl_up_sync(0xffffffffu, head, d);
+      if (lane >= d && !head) v += t;
+      if (lane >= d) head |= th;
+    }
+  }
+  const VT prev = __shfl_up_sync(0xffffffffu, v, 1);
+  if (in && !through) acc[f0] += prev;
 }
 
 template <typename VT, typename ValT>
 __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsParams p) {
+  using AT = typename XsVal<ValT>::AT;
   constexpr int S = 1 << XsCfg<VT>::kSliceBits;
+  constexpr int kSlot = xs_slot_elems<VT>();
   constexpr int NX = XsCfg<VT>::kBuffers;
+  constexpr uint32_t kRows = XsCfg<VT>::kRows;
   extern __shared__ __align__(128) unsigned char smem[];
-  VT* xb = reinterpret_cast<VT*>(smem);  // [NX][S]
-  VT* acc = xb + NX * S;                 // [kRows]
-  uint64_t* full = reinterpret_cast<uint64_t*>(acc + XsCfg<VT>::kRows);
+  VT* xb = reinterpret_cast<VT*>(smem);  // [NX][kSlot]
+  VT* acc = xb + NX * kSlot;             // [kRows + 32 * kXsWarps]
+  uint64_t* full = reinterpret_cast<uint64_t*>(acc + xs_acc_elems<VT>());
   uint64_t* empty = full + NX;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NX);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < NX) xb[threadIdx.x * kSlot + S] = VT(0);  // the zero column of each slot
   if (threadIdx.x == 0) {
     for (int b = 0; b < NX; ++b) {
       mbar_init(&full[b], 1);
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
         const int width = static_cast<int>((p.N - c0 < S ? p.N - c0 : static_cast<int64_t>(S)));
         constexpr int kVec = 16 / sizeof(VT);
         const int wb = width / kVec * kVec;  // by bulk copy; the rest (< 16 bytes) by this thread
-        VT* dst = xb + b * S;
+        VT* dst = xb + b * kSlot;
         const VT* src = static_cast<const VT*>(p.x) + c0;
         if (wb < width) {
           for (int k = wb; k < width; ++k) dst[k] = src[k];
@@ -321,13 +327,15 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
   }
 
   // ------------------------------------------------------------- consumers
-  // Each warp keeps kDepth chunks in registers: while one is summed, the
-  // others are in flight, across slice boundaries (a warp often has one chunk
-  // per slice).  Slice i's buffer is waited for before its first chunk is
+  // Each warp keeps kDepth groups in registers: while one is summed, the
+  // others are in flight, across slice boundaries (a warp often has one group
+  // per slice).  Slice i's buffer is waited for before its first group is
   // summed and released after its last; slices without entries of this warp
   // are waited for and released in turn, so every warp arrives once per slice.
   constexpr int D = XsCfg<VT>::kDepth;
   VT* y = static_cast<VT*>(p.y);
+  VT* scratch = acc + kRows + 32 * warp;
+  const uint32_t pad = ((kRows + 32u * warp + lane) << kXsColBits) | static_cast<uint32_t>(S);
   uint32_t v = 0;  // slices visited by this CTA, as counted by the producer
   bool ok = true;
   for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
@@ -336,21 +344,23 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
     const int32_t r_lo = p.warp_row[g] - tr0, r_hi = p.warp_row[g + 1] - tr0;
     const int i0 = p.tl_off[t], i1 = p.tl_off[t + 1];
     for (int32_t r = r_lo + lane; r < r_hi; r += 32) acc[r] = VT(0);
+    scratch[lane] = VT(0);
     __syncwarp();
     XsWindow win;
     xs_window_load(p, g, i1, i0, lane, win);
     XsPos q[D];
-    XsChunk<VT> k[D];
+    XsGroup<AT> k[D];
     q[0] = xs_next_slice(p, g, i0 - 1, i1, lane, win);
 #pragma unroll
     for (int d = 1; d < D; ++d) q[d] = xs_next(p, g, q[d - 1], i1, lane, win);
 #pragma unroll
     for (int d = 0; d < D; ++d)
-      if (q[d].i >= 0) xs_load<VT, ValT>(p, q[d].st, q[d].len, q[d].c, lane, k[d]);
-    int i = i0;           // next slice to wait for
-    bool held = false;    // slice i - 1 is waited for and not yet released
+      if (q[d].i >= 0) xs_load<ValT>(p, q[d], lane, pad, k[d]);
+    int i = i0;         // next slice to wait for
+    bool held = false;  // slice i - 1 is waited for and not yet released
+    uint32_t f0 = 0;    // accumulator of this lane's first entry in the current cell
     while (q[0].i >= 0) {
-      const XsChunk<VT> cur = k[0];
+      const XsGroup<AT> cur = k[0];
       const XsPos qc = q[0];
 #pragma unroll
       for (int d = 0; d + 1 < D; ++d) {
@@ -358,8 +368,8 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
         q[d] = q[d + 1];
       }
       q[D - 1] = xs_next(p, g, q[D - 1], i1, lane, win);
-      if (q[D - 1].i >= 0) xs_load<VT, ValT>(p, q[D - 1].st, q[D - 1].len, q[D - 1].c, lane, k[D - 1]);
-      while (i <= qc.i) {  // wait for slices up to this chunk's, releasing the empty ones
+      if (q[D - 1].i >= 0) xs_load<ValT>(p, q[D - 1], lane, pad, k[D - 1]);
+      while (i <= qc.i) {  // wait for slices up to this group's, releasing the empty ones
         if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
         if (ok) {
           ok = mbar_wait_bounded(&full[v % NX], (v / NX) & 1u, p.status);
@@ -370,7 +380,15 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
         ++i;
         ++v;
       }
-      if (ok) xs_compute<VT>(cur, xb + ((v - 1) % NX) * S, acc, lane);
+      if (ok) {
+        const int32_t L = xs_steps(qc.n);
+        if (qc.s0 == 0) f0 = cur.id[0] >> kXsColBits;
+        xs_compute<VT, AT>(cur, L - qc.s0 < kXsSteps ? L - qc.s0 : kXsSteps, xb + ((v - 1) % NX) * kSlot, acc);
+        if (qc.s0 + kXsSteps >= L) {  // the cell's last group
+          if (qc.cut) xs_combine<VT>(qc.cut, f0, acc, scratch, lane);
+          __syncwarp();  // the next cell may give this cell's rows to other lanes
+        }
+      }
     }
     while (i < i1) {  // slices after this warp's last entries
       if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
@@ -424,12 +442,19 @@ __global__ void xs_key_kernel(const int32_t* __restrict__ rowptr, const int32_t*
   atomicAdd(counts + key, 1);
 }
 
-// Place sorted entry i at seg_start[key] + (i - first sorted index of key).
+// Place sorted entry i (rank e of n in its cell) in its lane's run: the cell's
+// n entries are cut into 32 contiguous runs, the first rem = n - 32 (L - 1) of
+// L entries and the rest of L - 1, and run entry j of lane l goes to slot
+// seg_start + 32 j + l.  An entry whose row continues in the next lane's run
+// accumulates into the lane's scratch sum (kRows + 32 w + l, w the warp range
+// within the tile), every other entry into its tile-local row; the lane's last
+// entry sets cut bit l when its row continues.
 __global__ void xs_scatter_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals, int64_t Z,
-                                  const int32_t* __restrict__ seg_start, const int32_t* __restrict__ ustart,
-                                  const int32_t* __restrict__ col, const void* __restrict__ val, int vbytes,
-                                  const int32_t* __restrict__ tile_row, int sbits, int32_t nS,
-                                  uint32_t* __restrict__ idx_out, void* __restrict__ val_out) {
+                                  const int32_t* __restrict__ seg_start, const int32_t* __restrict__ seg_len,
+                                  const int32_t* __restrict__ ustart, const int32_t* __restrict__ col,
+                                  const void* __restrict__ val, int vbytes, const int32_t* __restrict__ tile_row,
+                                  int sbits, int32_t nS, int32_t rows_per_tile, uint32_t* __restrict__ idx_out,
+                                  void* __restrict__ val_out, uint32_t* __restrict__ cut_out) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= Z) return;
   const uint64_t k = keys[i];
@@ -437,15 +462,31 @@ __global__ void xs_scatter_kernel(const uint64_t* __restrict__ keys, const int32
   const int32_t row = static_cast<int32_t>(k >> 32);
   const int32_t e = vals[i];
   const int32_t g = static_cast<int32_t>(key / static_cast<uint32_t>(nS));
-  const int32_t t = g / kXsWarps;
-  const int64_t pos = static_cast<int64_t>(seg_start[key]) + (i - ustart[key]);
-  idx_out[pos] = (static_cast<uint32_t>(row - tile_row[t]) << sbits) | (static_cast<uint32_t>(col[e]) & ((1u << sbits) - 1u));
+  const int32_t t = g / kXsWarps, w = g % kXsWarps;
+  const int32_t first = ustart[key];
+  const int32_t rank = static_cast<int32_t>(i - first), n = seg_len[key];
+  const int32_t L = (n + 31) / 32, rem = n - 32 * (L - 1);
+  int32_t l, j;
+  if (rank < rem * L) {
+    l = rank / L;
+    j = rank % L;
+  } else {  // L >= 2 here
+    l = rem + (rank - rem * L) / (L - 1);
+    j = (rank - rem * L) % (L - 1);
+  }
+  const int32_t next = l * (L - 1) + (l < rem ? l : rem) + (l < rem ? L : L - 1);  // first rank of lane l + 1
+  const bool crosses = next < n && static_cast<int32_t>(keys[first + next] >> 32) == row;
+  const uint32_t acc = crosses ? static_cast<uint32_t>(rows_per_tile + 32 * w + l)
+                               : static_cast<uint32_t>(row - tile_row[t]);
+  const int64_t pos = static_cast<int64_t>(seg_start[key]) + 32 * static_cast<int64_t>(j) + l;
+  idx_out[pos] = (acc << kXsColBits) | (static_cast<uint32_t>(col[e]) & ((1u << sbits) - 1u));
   if (vbytes == 8)
     static_cast<double*>(val_out)[pos] = static_cast<const double*>(val)[e];
   else if (vbytes == 4)
     static_cast<float*>(val_out)[pos] = static_cast<const float*>(val)[e];
   else
     static_cast<uint16_t*>(val_out)[pos] = static_cast<const uint16_t*>(val)[e];
+  if (crosses && rank == next - 1) atomicOr(cut_out + key, 1u << l);
 }
 
 int bit_width_u64(uint64_t v) {
@@ -470,6 +511,7 @@ maxe_status xs_launch(const maxe_handle* h, const void* x, void* y, const int32_
   p.val = h->xs_val;
   p.seg_start = h->xs_seg_start;
   p.seg_len = h->xs_seg_len;
+  p.seg_cut = h->xs_seg_cut;
   p.tile_row = h->xs_tile_row;
   p.warp_row = h->xs_warp_row;
   p.tl_off = h->xs_tl_off;
@@ -590,7 +632,7 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool* built) {
   // ---- device arrays of the format
   uint32_t* idx = static_cast<uint32_t*>(al.get(sizeof(uint32_t) * (Zp + kXsSlack)));
   void* xval = al.get(static_cast<size_t>(vb) * (Zp + kXsSlack));
-  int32_t* d_seg = static_cast<int32_t*>(al.get(sizeof(int32_t) * 2 * cells));
+  int32_t* d_seg = static_cast<int32_t*>(al.get(sizeof(int32_t) * 3 * cells));
   int32_t* d_ustart = scratch.get<int32_t>(cells);
   int32_t* d_tl = static_cast<int32_t*>(al.get(sizeof(int32_t) * (tl_off.size() + std::max<size_t>(tl_slice.size(), 1))));
   if (!idx || !xval || !d_seg || !d_ustart || !d_tl) {
@@ -601,6 +643,7 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool* built) {
     return fail(MAXE_ERR_OOM);
   }
   int32_t* d_len = d_seg + cells;
+  uint32_t* d_cut = reinterpret_cast<uint32_t*>(d_seg + 2 * cells);
   MAXE_CUDA_TRY(cudaMemcpyAsync(d_seg, seg_start.data(), sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
   MAXE_CUDA_TRY(cudaMemcpyAsync(d_len, cnt.data(), sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
   MAXE_CUDA_TRY(cudaMemcpyAsync(d_ustart, ustart.data(), sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
@@ -608,26 +651,28 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool* built) {
   if (!tl_slice.empty())
     MAXE_CUDA_TRY(cudaMemcpyAsync(d_tl + tl_off.size(), tl_slice.data(), sizeof(int32_t) * tl_slice.size(),
                                   cudaMemcpyHostToDevice, st));
+  MAXE_CUDA_TRY(cudaMemsetAsync(d_cut, 0, sizeof(uint32_t) * cells, st));
   MAXE_CUDA_TRY(cudaMemsetAsync(idx, 0, sizeof(uint32_t) * (Zp + kXsSlack), st));
   MAXE_CUDA_TRY(cudaMemsetAsync(xval, 0, static_cast<size_t>(vb) * (Zp + kXsSlack), st));
   // ---- stable sort by (warp range, slice); entries keep CSR order inside a cell
   MAXE_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, Z, bit_width_u64(static_cast<uint64_t>(cells - 1)), rs,
                             st));
   xs_scatter_kernel<<<static_cast<unsigned>(ceil_div(Z, 256)), 256, 0, st>>>(
-      keys, vals, Z, d_seg, d_ustart, h->col, h->val, vb, d_trow, SB, nS, idx, xval);
+      keys, vals, Z, d_seg, d_len, d_ustart, h->col, h->val, vb, d_trow, SB, nS, RMAX, idx, xval, d_cut);
   MAXE_CUDA_TRY(cudaGetLastError());
   MAXE_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors and scratch go out of scope
   h->xs_idx = idx;
   h->xs_val = xval;
   h->xs_seg_start = d_seg;
   h->xs_seg_len = d_len;
+  h->xs_seg_cut = d_cut;
   h->xs_tile_row = d_trow;
   h->xs_warp_row = d_wrow;
   h->xs_tl_off = d_tl;
   h->xs_tl_slice = d_tl + tl_off.size();
   h->xs_ntiles = ntiles;
   h->xs_nS = nS;
-  h->xs_bytes = static_cast<int64_t>(Zp) * (4 + vb);
+  h->xs_bytes = static_cast<int64_t>(Zp) * (4 + vb) + 12 * cells;
   *built = true;
   return MAXE_OK;
 }
@@ -660,6 +705,7 @@ void xslice_release(maxe_handle* h) {
   al.put(h->xs_warp_row);
   al.put(h->xs_tile_row);
   h->xs_tl_off = h->xs_tl_slice = h->xs_seg_start = h->xs_seg_len = nullptr;
+  h->xs_seg_cut = nullptr;
   h->xs_warp_row = h->xs_tile_row = nullptr;
   h->xs_idx = nullptr;
   h->xs_val = nullptr;
