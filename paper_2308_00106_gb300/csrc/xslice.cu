@@ -54,14 +54,12 @@ struct XsCfg<float> {
   static constexpr int kSliceBits = 14;  // 16384 columns, 64 KB
   static constexpr int kBuffers = 3;     // slices in the ring: two loads in flight while one is read
   static constexpr int kRows = 8192;     // rows per tile
-  static constexpr int kDepth = 2;       // register groups per warp (one summed, one in flight)
 };
 template <>
 struct XsCfg<double> {
   static constexpr int kSliceBits = 13;  // 8192 columns, 64 KB
   static constexpr int kBuffers = 2;
   static constexpr int kRows = 8192;
-  static constexpr int kDepth = 2;
 };
 
 // One slot of the ring: the slice and 16 bytes after it, the first element of
@@ -200,20 +198,20 @@ __device__ __forceinline__ XsPos xs_next(const XsParams& p, int64_t g, const XsP
   return xs_next_slice(p, g, q.i, i_end, lane, w);
 }
 
-// Load the group's steps of this lane's run; steps past the run hold `pad`
-// (the lane's scratch accumulator, the zero column) and value 0.
+// Load the group's steps (those of the cell's L steps) of this lane's run.
+// The slots past a lane's run hold a pad entry (the lane's scratch sum, the
+// zero column, value 0), so every lane loads every step unconditionally.
 template <typename ValT>
-__device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int lane, uint32_t pad,
+__device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int lane,
                                         XsGroup<typename XsVal<ValT>::AT>& k) {
-  using AT = typename XsVal<ValT>::AT;
-  const int32_t L = xs_steps(q.n);
-  const int32_t len = L - (lane >= q.n - 32 * (L - 1) ? 1 : 0);  // entries of this lane's run
+  const int32_t ns = xs_steps(q.n) - q.s0;
   const int64_t base = static_cast<int64_t>(q.st) + static_cast<int64_t>(q.s0) * 32 + lane;
 #pragma unroll
   for (int j = 0; j < kXsSteps; ++j) {
-    const bool v = q.s0 + j < len;
-    k.id[j] = v ? __ldcs(p.idx + base + 32 * j) : pad;
-    k.a[j] = v ? XsVal<ValT>::ld(p.val, base + 32 * j) : AT(0);
+    if (j < ns) {
+      k.id[j] = __ldcs(p.idx + base + 32 * j);
+      k.a[j] = XsVal<ValT>::ld(p.val, base + 32 * j);
+    }
   }
 }
 
@@ -236,33 +234,28 @@ __device__ __forceinline__ void xs_compute(const XsGroup<AT>& k, int ns, const V
 // rows.  cut bit l: lane l's last row continues in lane l + 1 (its entries of
 // that row went to scratch[l]).  f0: the accumulator of the lane's first
 // entry -- a row, or the lane's scratch when the lane's first row continues
-// (then the lane holds that row only).  The lane whose first row came from the
-// previous lane and ends in it adds the chain's scratch sums, in lane order.
+// (then the lane holds that row only and the row runs through it).  The lane
+// whose first row came from the previous lane and ends in it reads the
+// chain's scratch sums from shared memory, last lane first, and adds them to
+// the row; then the lanes clear their scratch sums.
 template <typename VT>
 __device__ __forceinline__ void xs_combine(uint32_t cut, uint32_t f0, VT* __restrict__ acc,
                                            VT* __restrict__ scratch, int lane) {
   constexpr uint32_t kRows = XsCfg<VT>::kRows;
-  const bool out = (cut >> lane) & 1u;
   const bool in = lane > 0 && ((cut >> (lane - 1)) & 1u);
-  VT v = VT(0);
-  if (out) {
-    v = scratch[lane];
-    scratch[lane] = VT(0);
-  }
-  const bool through = in && f0 >= kRows;  // one row, continuing on both sides
-  if (__ballot_sync(0xffffffffu, through)) {
-    // segmented inclusive scan: a lane the row runs through adds the sum so far
-    int head = through ? 0 : 1;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const VT t = __shfl_up_sync(0xffffffffu, v, d);
-      const int th = __shfl_up_sync(0xffffffffu, head, d);
-      if (lane >= d && !head) v += t;
-      if (lane >= d) head |= th;
+  const bool through = in && f0 >= kRows;
+  const unsigned thr = __ballot_sync(0xffffffffu, through);
+  __syncwarp();  // every lane's scratch sum is written
+  if (in && !through) {
+    VT sum = VT(0);
+    for (int m = lane - 1;; --m) {  // ends at the chain's first lane (not run through; lane 0 never is)
+      sum += scratch[m];
+      if (!((thr >> m) & 1u)) break;
     }
+    acc[f0] += sum;
   }
-  const VT prev = __shfl_up_sync(0xffffffffu, v, 1);
-  if (in && !through) acc[f0] += prev;
+  __syncwarp();  // read before cleared
+  if ((cut >> lane) & 1u) scratch[lane] = VT(0);
 }
 
 template <typename VT, typename ValT>
@@ -327,15 +320,13 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
   }
 
   // ------------------------------------------------------------- consumers
-  // Each warp keeps kDepth groups in registers: while one is summed, the
-  // others are in flight, across slice boundaries (a warp often has one group
-  // per slice).  Slice i's buffer is waited for before its first group is
+  // Each warp keeps two groups in registers: while one is summed, the other
+  // is in flight, across slice boundaries (a warp often has one group per
+  // slice).  Slice i's buffer is waited for before its first group is
   // summed and released after its last; slices without entries of this warp
   // are waited for and released in turn, so every warp arrives once per slice.
-  constexpr int D = XsCfg<VT>::kDepth;
   VT* y = static_cast<VT*>(p.y);
   VT* scratch = acc + kRows + 32 * warp;
-  const uint32_t pad = ((kRows + 32u * warp + lane) << kXsColBits) | static_cast<uint32_t>(S);
   uint32_t v = 0;  // slices visited by this CTA, as counted by the producer
   bool ok = true;
   for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
@@ -348,27 +339,20 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
     __syncwarp();
     XsWindow win;
     xs_window_load(p, g, i1, i0, lane, win);
-    XsPos q[D];
-    XsGroup<AT> k[D];
-    q[0] = xs_next_slice(p, g, i0 - 1, i1, lane, win);
-#pragma unroll
-    for (int d = 1; d < D; ++d) q[d] = xs_next(p, g, q[d - 1], i1, lane, win);
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-      if (q[d].i >= 0) xs_load<ValT>(p, q[d], lane, pad, k[d]);
+    // Two register groups with fixed roles, A and B, summed in turn: while one
+    // is summed the other's loads are in flight.  (Rotating one array of
+    // groups would copy registers whose loads are still in flight, and the
+    // copy waits for them.)
+    XsGroup<AT> kA, kB;
+    XsPos qA = xs_next_slice(p, g, i0 - 1, i1, lane, win);
+    XsPos qB = xs_next(p, g, qA, i1, lane, win);
+    if (qA.i >= 0) xs_load<ValT>(p, qA, lane, kA);
+    if (qB.i >= 0) xs_load<ValT>(p, qB, lane, kB);
+    XsPos qn = xs_next(p, g, qB, i1, lane, win);  // the group after the two in registers
     int i = i0;         // next slice to wait for
     bool held = false;  // slice i - 1 is waited for and not yet released
     uint32_t f0 = 0;    // accumulator of this lane's first entry in the current cell
-    while (q[0].i >= 0) {
-      const XsGroup<AT> cur = k[0];
-      const XsPos qc = q[0];
-#pragma unroll
-      for (int d = 0; d + 1 < D; ++d) {
-        k[d] = k[d + 1];
-        q[d] = q[d + 1];
-      }
-      q[D - 1] = xs_next(p, g, q[D - 1], i1, lane, win);
-      if (q[D - 1].i >= 0) xs_load<ValT>(p, q[D - 1], lane, pad, k[D - 1]);
+    auto sum_group = [&](const XsPos& qc, const XsGroup<AT>& grp) {
       while (i <= qc.i) {  // wait for slices up to this group's, releasing the empty ones
         if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
         if (ok) {
@@ -382,13 +366,24 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
       }
       if (ok) {
         const int32_t L = xs_steps(qc.n);
-        if (qc.s0 == 0) f0 = cur.id[0] >> kXsColBits;
-        xs_compute<VT, AT>(cur, L - qc.s0 < kXsSteps ? L - qc.s0 : kXsSteps, xb + ((v - 1) % NX) * kSlot, acc);
+        if (qc.s0 == 0) f0 = grp.id[0] >> kXsColBits;
+        xs_compute<VT, AT>(grp, L - qc.s0 < kXsSteps ? L - qc.s0 : kXsSteps, xb + ((v - 1) % NX) * kSlot, acc);
         if (qc.s0 + kXsSteps >= L) {  // the cell's last group
           if (qc.cut) xs_combine<VT>(qc.cut, f0, acc, scratch, lane);
           __syncwarp();  // the next cell may give this cell's rows to other lanes
         }
       }
+    };
+    while (qA.i >= 0) {
+      sum_group(qA, kA);
+      qA = qn;
+      if (qA.i >= 0) xs_load<ValT>(p, qA, lane, kA);
+      qn = xs_next(p, g, qn, i1, lane, win);
+      if (qB.i < 0) break;
+      sum_group(qB, kB);
+      qB = qn;
+      if (qB.i >= 0) xs_load<ValT>(p, qB, lane, kB);
+      qn = xs_next(p, g, qn, i1, lane, win);
     }
     while (i < i1) {  // slices after this warp's last entries
       if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
@@ -487,6 +482,10 @@ __global__ void xs_scatter_kernel(const uint64_t* __restrict__ keys, const int32
   else
     static_cast<uint16_t*>(val_out)[pos] = static_cast<const uint16_t*>(val)[e];
   if (crosses && rank == next - 1) atomicOr(cut_out + key, 1u << l);
+  if (rank == n - 1)  // the last step's slots past the runs: pad entries (value 0, zeroed before)
+    for (int32_t q = rem; q < 32; ++q)
+      idx_out[static_cast<int64_t>(seg_start[key]) + 32 * static_cast<int64_t>(L - 1) + q] =
+          (static_cast<uint32_t>(rows_per_tile + 32 * w + q) << kXsColBits) | (1u << sbits);
 }
 
 int bit_width_u64(uint64_t v) {
