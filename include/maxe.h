@@ -197,7 +197,8 @@ MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, c
 /* Kernel variants of the handle, as chosen by MAXE_AUTOTUNE / MAXE_ITEMS16 /
  * MAXE_SPMM_LANES at creation: *items = entries per lane of the SpMV variant
  * (8 or 16), plus 0x100 when SpMM uses columns across lanes, plus 0x200 when
- * SpMV uses the x-sliced form (MAXE_XSLICE).  items: (host). */
+ * SpMV uses the x-sliced form (MAXE_XSLICE), plus 0x400 when that form's cells
+ * are large enough for its L2 prefetch cursor.  items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;

@@ -203,7 +203,8 @@ maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view, const int32_t*
 
 maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
   if (!h || !items) return MAXE_ERR_INVALID;
-  *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0) | (h->xs_use ? 0x200 : 0);
+  *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0) | (h->xs_use ? 0x200 : 0) |
+           (h->xs_use && h->xs_prefetch ? 0x400 : 0);
   return MAXE_OK;
 }
 

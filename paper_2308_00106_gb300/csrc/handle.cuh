@@ -48,6 +48,7 @@ struct maxe_handle {
   int32_t xs_ntiles = 0, xs_nS = 0;
   int64_t xs_bytes = 0;
   int xs_use = 0;                          // SpMV (k = 1) takes the x-sliced kernel
+  int xs_prefetch = 0;                     // cells large enough for the L2 prefetch cursor
   int32_t* coo_row = nullptr;              // COO row index of every entry (MAXE_COO), else NULL
   void* coo_carry = nullptr;               // COO per-chunk partial sums and flags
   void* xbuf = nullptr;  // cols * k_cap vector elements

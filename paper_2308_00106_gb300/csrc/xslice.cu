@@ -98,6 +98,11 @@ struct XsParams {
   unsigned* status;
 };
 
+// Prefetch `bytes` at p (16-byte aligned, a multiple of 16) into L2; no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
@@ -215,6 +220,24 @@ __device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int l
   }
 }
 
+// With large cells (the entries of a warp in a slice span several groups) a
+// second cursor runs kXsAhead groups ahead of the loads and prefetches their
+// entries into L2, so the loads find them there; with small cells its
+// bookkeeping per group costs more than it hides.
+constexpr int kXsAhead = 4;
+constexpr int64_t kXsPrefetchCell = 2 * 32 * kXsSteps;  // mean entries per cell from which the cursor runs
+
+template <typename ValT>
+__device__ __forceinline__ void xs_prefetch(const XsParams& p, const XsPos& q, int lane) {
+  if (q.i < 0 || lane != 0) return;
+  const int32_t L = xs_steps(q.n);
+  const int32_t ns = L - q.s0 < kXsSteps ? L - q.s0 : kXsSteps;
+  const int64_t base = static_cast<int64_t>(q.st) + static_cast<int64_t>(q.s0) * 32;
+  prefetch_l2(p.idx + base, static_cast<uint32_t>(ns * 32 * 4));
+  prefetch_l2(static_cast<const unsigned char*>(p.val) + base * static_cast<int64_t>(sizeof(ValT)),
+              static_cast<uint32_t>(ns * 32 * sizeof(ValT)));
+}
+
 // acc[slot] += a * x[column] for the group's first ns steps.
 template <typename VT, typename AT>
 __device__ __forceinline__ void xs_compute(const XsGroup<AT>& k, int ns, const VT* __restrict__ xs,
@@ -258,7 +281,7 @@ __device__ __forceinline__ void xs_combine(uint32_t cut, uint32_t f0, VT* __rest
   if ((cut >> lane) & 1u) scratch[lane] = VT(0);
 }
 
-template <typename VT, typename ValT>
+template <typename VT, typename ValT, bool PF>
 __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsParams p) {
   using AT = typename XsVal<ValT>::AT;
   constexpr int S = 1 << XsCfg<VT>::kSliceBits;
@@ -349,6 +372,16 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
     if (qA.i >= 0) xs_load<ValT>(p, qA, lane, kA);
     if (qB.i >= 0) xs_load<ValT>(p, qB, lane, kB);
     XsPos qn = xs_next(p, g, qB, i1, lane, win);  // the group after the two in registers
+    XsWindow winp;  // the prefetch cursor, kXsAhead groups ahead of the loads (PF)
+    XsPos qp{-1, 0, 0, 0, 0u};
+    if constexpr (PF) {
+      xs_window_load(p, g, i1, i0, lane, winp);
+      qp = xs_next_slice(p, g, i0 - 1, i1, lane, winp);
+      for (int d = 0; d < 2 + kXsAhead; ++d) {
+        if (d >= 2) xs_prefetch<ValT>(p, qp, lane);
+        qp = xs_next(p, g, qp, i1, lane, winp);
+      }
+    }
     int i = i0;         // next slice to wait for
     bool held = false;  // slice i - 1 is waited for and not yet released
     uint32_t f0 = 0;    // accumulator of this lane's first entry in the current cell
@@ -379,11 +412,19 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
       qA = qn;
       if (qA.i >= 0) xs_load<ValT>(p, qA, lane, kA);
       qn = xs_next(p, g, qn, i1, lane, win);
+      if constexpr (PF) {
+        xs_prefetch<ValT>(p, qp, lane);
+        qp = xs_next(p, g, qp, i1, lane, winp);
+      }
       if (qB.i < 0) break;
       sum_group(qB, kB);
       qB = qn;
       if (qB.i >= 0) xs_load<ValT>(p, qB, lane, kB);
       qn = xs_next(p, g, qn, i1, lane, win);
+      if constexpr (PF) {
+        xs_prefetch<ValT>(p, qp, lane);
+        qp = xs_next(p, g, qp, i1, lane, winp);
+      }
     }
     while (i < i1) {  // slices after this warp's last entries
       if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
@@ -501,7 +542,11 @@ template <typename VT, typename ValT>
 maxe_status xs_launch(const maxe_handle* h, const void* x, void* y, const int32_t* yperm, cudaStream_t st) {
   static bool attr_set[64] = {};
   if (h->device >= 0 && h->device < 64 && !attr_set[h->device]) {
-    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmv_xslice_kernel<VT, ValT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmv_xslice_kernel<VT, ValT, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(xs_smem_bytes<VT>())));
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmv_xslice_kernel<VT, ValT, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(xs_smem_bytes<VT>())));
     attr_set[h->device] = true;
   }
@@ -523,7 +568,10 @@ maxe_status xs_launch(const maxe_handle* h, const void* x, void* y, const int32_
   p.yperm = yperm;
   p.status = h->status;
   const int grid = std::min(h->xs_ntiles, h->sms);
-  spmv_xslice_kernel<VT, ValT><<<grid, kXsThreads, xs_smem_bytes<VT>(), st>>>(p);
+  if (h->xs_prefetch)
+    spmv_xslice_kernel<VT, ValT, true><<<grid, kXsThreads, xs_smem_bytes<VT>(), st>>>(p);
+  else
+    spmv_xslice_kernel<VT, ValT, false><<<grid, kXsThreads, xs_smem_bytes<VT>(), st>>>(p);
   MAXE_CUDA_TRY(cudaGetLastError());
   return MAXE_OK;
 }
@@ -672,6 +720,9 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool* built) {
   h->xs_ntiles = ntiles;
   h->xs_nS = nS;
   h->xs_bytes = static_cast<int64_t>(Zp) * (4 + vb) + 12 * cells;
+  int64_t nonempty = 0;
+  for (int64_t k = 0; k < cells; ++k) nonempty += cnt[k] > 0;
+  h->xs_prefetch = nonempty > 0 && Z >= kXsPrefetchCell * nonempty ? 1 : 0;
   *built = true;
   return MAXE_OK;
 }

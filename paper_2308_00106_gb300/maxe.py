@@ -235,6 +235,10 @@ class Handle:
         """True when SpMV runs on the x-sliced form (MAXE_XSLICE, kept by the autotuner or forced)."""
         return bool(self._tuning() & 0x200)
 
+    def xslice_prefetch(self) -> bool:
+        """True when the x-sliced SpMV runs its L2 prefetch cursor (large cells)."""
+        return bool(self._tuning() & 0x400)
+
     def spmm_lanes(self) -> bool:
         """True when SpMM spreads the k columns across lanes (else column passes)."""
         return bool(self._tuning() & 0x100)

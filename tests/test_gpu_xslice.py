@@ -53,7 +53,7 @@ def test_xslice_many_tiles_per_cta(dtype):
     tiles and the slice ring's phases carry across them."""
     A = W.laplacian5(1700, dtype, "cuda")
     h = maxe.from_csr(A, xslice=True)
-    assert h.xslice()
+    assert h.xslice() and h.xslice_prefetch()  # natural order: large cells, the prefetch cursor runs
     x = W.vector(3, A.cols, dtype, "cuda")
     y = maxe.maxe_spmv(h, x)
     rp, co, va = A.numpy()
@@ -75,6 +75,7 @@ def test_xslice_powerlaw_deterministic_and_matches_csr():
     h = maxe.from_csr(A, rperm, cperm, xslice=True)
     hc = maxe.from_csr(A, rperm, cperm)
     assert h.xslice() and not hc.xslice()
+    assert not h.xslice_prefetch()  # permuted: ~100-entry cells, no prefetch cursor
     x = W.vector(4, A.cols, "f32", "cuda")
     y1 = maxe.maxe_spmv(h, x)
     assert torch.equal(maxe.maxe_spmv(h, x), y1)
