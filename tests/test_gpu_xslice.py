@@ -104,3 +104,33 @@ def test_xslice_autotune_keeps_the_faster_kernel():
     rows = np.random.default_rng(3).choice(A.rows, 2000, replace=False)
     y = maxe.maxe_spmv(h, x)
     assert rel_l2(y.cpu().numpy()[rows], oracle.spmv_rows(rp, co, va, code("f32"), x.cpu().numpy(), rows)) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("permuted", [False, True])
+def test_xslice_pad_entries_keep_infinite_x_out_of_other_rows(dtype, permuted):
+    """The slots after the lane runs of a cell read the zero column after each
+    slice, not x: infinities in x reach only the rows that have entries in
+    those columns.  The infinities sit on the first column of every slice and
+    on the last column."""
+    lengths = np.random.default_rng(12).integers(0, 40, 5000)
+    A = W.from_lengths(12, lengths, 40000, dtype)
+    rperm, cperm = _perms(A, 13) if permuted else (None, None)
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, xslice=True)
+    assert h.xslice()
+    nrp, nco, nva = oracle_permuted(A, rperm, cperm)
+    sb = 13 if dtype == "f64" else 14
+    bad = np.unique(np.r_[np.arange(0, A.cols, 1 << sb), A.cols - 1])
+    vd = "f64" if dtype == "f64" else "f32"
+    xp = W.vector(14, A.cols, vd, "cuda")
+    xp[torch.as_tensor(bad, device="cuda")] = float("inf")
+    y = maxe.maxe_spmv(h, xp, permuted=True).cpu().numpy()
+    row_of = np.repeat(np.arange(A.rows), np.diff(nrp))
+    hit = np.zeros(A.rows, dtype=bool)
+    hit[row_of[np.isin(nco, bad)]] = True
+    assert hit.any() and (~hit).sum() > A.rows // 2
+    assert np.isfinite(y[~hit]).all()
+    x0 = xp.cpu().numpy().copy()
+    x0[bad] = 0.0
+    ref = oracle.spmv(A.rows, nrp, nco, nva, code(dtype), x0)
+    assert rel_l2(y[~hit], ref[~hit]) <= TOL[dtype]
