@@ -18,8 +18,11 @@
 //   - every entry adds a * x[col] to its row's accumulator.  A row that a lane
 //     boundary cuts is split: the entries before the cut go to the lane's own
 //     scratch accumulator, the ones after it to the row, and after the cell the
-//     scratch sums are added to the row by the lane that holds the row's last
-//     run (a shuffle, or a segmented scan when a row crosses a whole lane);
+//     lane that holds the row's last run reads the scratch sums of the lanes
+//     the row came through from shared memory and adds them to the row;
+//   - two register groups of 8 steps per warp, one summed while the other
+//     loads; with large cells a second cursor prefetches the entries four
+//     groups ahead into L2;
 //   - at the end of the tile every warp writes its rows of y (through rperm
 //     when y is wanted in the original space).
 //
