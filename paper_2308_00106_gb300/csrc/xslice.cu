@@ -144,8 +144,9 @@ struct XsGroup {
 };
 
 // Position of a group in a warp's stream over the tile's slices: slice index i
-// (into tl_slice), the cell [st, st + n) with its cut mask, and the first step
-// s0 of the group; i = -1 past the end.  The cells of 32 slices at a time sit
+// (into tl_slice), the cell (n entries in the 32 * ceil(n / 32) slots from
+// slot st) with its cut mask, and the first step s0 of the group; i = -1 past
+// the end.  The cells of 32 slices at a time sit
 // in the lanes (lane l: slice index base + l), so finding the next slice with
 // entries is a ballot.
 struct XsPos {
@@ -481,7 +482,7 @@ __global__ void xs_key_kernel(const int32_t* __restrict__ rowptr, const int32_t*
   atomicAdd(counts + key, 1);
 }
 
-// Place sorted entry i (rank e of n in its cell) in its lane's run: the cell's
+// Place sorted entry i (rank `rank` of n in its cell) in its lane's run: the cell's
 // n entries are cut into 32 contiguous runs, the first rem = n - 32 (L - 1) of
 // L entries and the rest of L - 1, and run entry j of lane l goes to slot
 // seg_start + 32 j + l.  An entry whose row continues in the next lane's run
