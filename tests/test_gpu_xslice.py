@@ -47,14 +47,14 @@ def test_xslice_spmv_against_oracle(kind, dtype):
     assert rel_l2(yp.cpu().numpy(), oracle.spmv(A.rows, nrp, nco, nva, code(dtype), xp.cpu().numpy())) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
 def test_xslice_many_tiles_per_cta(dtype):
     """More row tiles than SMs (the 5-point Laplacian, 2.9M rows): CTAs loop over
     tiles and the slice ring's phases carry across them."""
     A = W.laplacian5(1700, dtype, "cuda")
     h = maxe.from_csr(A, xslice=True)
     assert h.xslice() and h.xslice_prefetch()  # natural order: large cells, the prefetch cursor runs
-    x = W.vector(3, A.cols, dtype, "cuda")
+    x = W.vector(3, A.cols, "f64" if dtype == "f64" else "f32", "cuda")
     y = maxe.maxe_spmv(h, x)
     rp, co, va = A.numpy()
     rows = np.random.default_rng(1).choice(A.rows, 4000, replace=False)
