@@ -92,7 +92,9 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * warps own row ranges and read their entries slice by slice, gathering x from
  * shared memory instead of L2 (one L2 request per nonzero on a randomly
  * permuted matrix is what bounds the CSR kernel there).  Costs 4 + value-size
- * bytes per entry more memory and a synchronising build.  MAXE_AUTOTUNE builds
+ * bytes per entry more memory (each (row range, slice) cell padded to 32
+ * entries, plus 12 bytes of descriptor per cell) and a synchronising build.
+ * MAXE_AUTOTUNE builds
  * it too when its x traffic would stay under four times the matrix, and keeps
  * it only if it times faster than the CSR kernel.  Ignored with
  * MAXE_EQUAL_ROWS.  Deterministic. */
