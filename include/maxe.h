@@ -94,10 +94,9 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * permuted matrix is what bounds the CSR kernel there).  Costs 4 + value-size
  * bytes per entry more memory (each (row range, slice) cell padded to 32
  * entries, plus 12 bytes of descriptor per cell) and a synchronising build.
- * MAXE_AUTOTUNE builds
- * it too when its x traffic would stay under four times the matrix, and keeps
- * it only if it times faster than the CSR kernel.  Ignored with
- * MAXE_EQUAL_ROWS.  Deterministic. */
+ * MAXE_AUTOTUNE builds it too when its x traffic would stay under four times
+ * the matrix, and keeps it only if it times faster than the CSR kernel.
+ * Ignored with MAXE_EQUAL_ROWS.  Deterministic. */
 #define MAXE_XSLICE 0x80u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
