@@ -187,6 +187,11 @@ class Server:
                 r.result = (float(r.bufs["lam"].item()), r.bufs["u"].clone(), r.bufs["u0"])
             else:
                 r.result = r.bufs["Y"].contiguous()
+            # The copies above are queued on the current stream, but the buffers
+            # belong to adm_stream: once dropped, the caching allocator may hand
+            # them to the next admission on adm_stream, so that stream must not
+            # run ahead of the copies.
+            self.adm_stream.wait_stream(torch.cuda.current_stream())
         r.bufs = {}
 
     # ------------------------------------------------------------ the loop
