@@ -48,23 +48,66 @@ def alg_bytes(M, N, Z, vbytes, xbytes, ybytes, k=1):
     return Z * (vbytes + 4) + (M + 1) * 4 + M * k * ybytes + N * k * xbytes
 
 
-def traffic_from_profile(name):
-    """dram bytes per launch from a committed ncu summary (line 'traffic_bytes_per_launch: N')."""
-    p = os.path.join(ROOT, "profiles", name)
+# The ncu DRAM traffic quoted in the roofline belongs to one revision of a
+# kernel's source: each record under profiles/ carries the SHA-256 of the
+# source files it was measured on, and a record whose hash differs from the
+# current files is not quoted (traffic null).
+KERNEL_SOURCES = {
+    "spmv_xslice_kernel": ["paper_2308_00106_gb300/csrc/xslice.cu", "paper_2308_00106_gb300/csrc/internal.cuh"],
+    "spmm_warp_kernel": ["paper_2308_00106_gb300/csrc/spmv_warp.cuh", "paper_2308_00106_gb300/csrc/spmv.cu",
+                         "paper_2308_00106_gb300/csrc/internal.cuh"],
+}
+PROFILE_RECORD = {"spmv_xslice_kernel": "spmv_xslice_powerlaw1M_f32.json",
+                  "spmm_warp_kernel": "spmv_warp_powerlaw1M_f32.json"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_from_record(kernel: str, profiles_dir=None):
+    """DRAM bytes per launch of `kernel` from its committed ncu record, or None
+    when there is none or it was measured on other sources."""
+    p = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), PROFILE_RECORD[kernel])
     if not os.path.exists(p):
-        return None, None
-    t, kernel_rev = None, None
-    for line in open(p):
-        if line.startswith("traffic_bytes_per_launch:"):
-            t = float(line.split(":", 1)[1])
-        if line.startswith("kernel_revision:"):
-            kernel_rev = line.split(":", 1)[1].strip()
-    return t, kernel_rev
+        return None
+    rec = json.load(open(p))
+    if rec.get("source_sha256") != kernel_source_hash(kernel):
+        return None
+    return float(rec["traffic_bytes_per_launch"])
 
 
-# bump a revision whenever that kernel changes: its committed ncu traffic then no longer applies
-KERNEL_REVISION = {"spmm_warp_kernel": "spmm_warp_kernel r3", "spmv_xslice_kernel": "spmv_xslice_kernel r5"}
-PROFILE_OF = {"spmm_warp_kernel": "spmv_warp_powerlaw1M_f32.md", "spmv_xslice_kernel": "spmv_xslice_powerlaw1M_f32.md"}
+def record_profile(csv_path: str, kernel: str, launch: int, command: str, workload: str, out_dir=None) -> dict:
+    """Write the ncu record of `kernel` (DRAM read + write bytes of its
+    `launch`-th captured launch, from `ncu -i REP --page raw --csv` output) with
+    the hash of the current sources."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    head = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "dram__bytes_read.sum" in r)
+    cols, units = rows[head], rows[head + 1]
+    data = [r for r in rows[head + 2:] if len(r) == len(cols) and kernel in r[cols.index("Kernel Name")]]
+    r = data[launch]
+    scale = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "nsecond": 1, "usecond": 1e3, "msecond": 1e6}
+
+    def val(name):
+        i = cols.index(name)
+        return float(r[i].replace(",", "")) * scale[units[i].strip().lower()]
+
+    rec = {"kernel": kernel, "kernel_name": r[cols.index("Kernel Name")], "workload": workload,
+           "traffic_bytes_per_launch": val("dram__bytes_read.sum") + val("dram__bytes_write.sum"),
+           "dram_read_bytes": val("dram__bytes_read.sum"), "dram_write_bytes": val("dram__bytes_write.sum"),
+           "duration_us_under_ncu": val("gpu__time_duration.sum") / 1e3 if "gpu__time_duration.sum" in cols else None,
+           "note": "ncu times are serialised and cold-cache; the bench's CUDA-event timing is the performance number",
+           "source_files": KERNEL_SOURCES[kernel], "source_sha256": kernel_source_hash(kernel), "command": command}
+    with open(os.path.join(out_dir or os.path.join(ROOT, "profiles"), PROFILE_RECORD[kernel]), "w") as fh:
+        json.dump(rec, fh, indent=1)
+        fh.write("\n")
+    return rec
 
 
 class Clocks:
@@ -174,12 +217,14 @@ def make_workload(name, seed, device):
 
 def timed_steps(step, K, W, world, graph_len=50):
     """W warm-up steps, then exactly K steps (CUDA graph replays of graph_len
-    steps plus a remainder) bracketed by barrier + synchronize; returns ms/step."""
+    steps plus a remainder, when K >= graph_len > 1; else K eager launches)
+    bracketed by barrier + synchronize; returns (ms per step, graph replayed)."""
     for _ in range(W):
         step()
     torch.cuda.synchronize()
     g = None
-    if graph_len > 1 and K >= graph_len:
+    graph_len = min(graph_len, K)
+    if graph_len > 1:
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -205,7 +250,7 @@ def timed_steps(step, K, W, world, graph_len=50):
     torch.cuda.synchronize()
     barrier(world)
     ms = e0.elapsed_time(e1)
-    return max_over_ranks(ms, world) / K
+    return max_over_ranks(ms, world) / K, g is not None
 
 
 def seed_sweep(A, x, args, world, tune):
@@ -234,7 +279,7 @@ def seed_sweep(A, x, args, world, tune):
             e1.record()
             torch.cuda.synchronize()
             cold = e0.elapsed_time(e1)
-        ms = timed_steps(lambda: maxe.maxe_spmv(h, xp, y, permuted=True), 200, 3, world, graph_len=50)
+        ms, _ = timed_steps(lambda: maxe.maxe_spmv(h, xp, y, permuted=True), 200, 3, world, graph_len=50)
         gbs.append(by / (ms * 1e-3) / 1e9)
         ents.append(maxe.maxe_nnz_entropy(h, 64, 64, counts=False)[0])
         h.close()
@@ -412,24 +457,23 @@ def run_reference(args):
     }))
 
 
-def run_batched(args):
+def batched_measure(seed, count, steps, warmup, world, tune, profile=False):
     """256 uneven matrices with 1..16 right-hand sides: one persistent launch
-    (CUDA graph) against 256 per-matrix launches of the same kernel family."""
+    (CUDA graph) against per-matrix launches of the same kernel family.  Returns
+    the measurement as a dict (None when profiling)."""
     from paper_2308_00106_gb300 import maxe
     from paper_2308_00106_gb300 import workloads as W
 
-    rank, world, local = dist_setup(args)
-    maxe.load(build_if_missing=(rank == 0))
     t0 = time.perf_counter()
-    mats, ks = W.batched_set(args.seed, count=args.batch_count, device="cuda")
+    mats, ks = W.batched_set(seed, count=count, device="cuda")
     t_gen = time.perf_counter() - t0
     hs, Xs, Ys, Yp = [], [], [], []
     t0 = time.perf_counter()
     for m, (A, k) in enumerate(zip(mats, ks)):
-        r = maxe.maxe_build_permutation(args.seed + m, A.rows, 0)
-        c = maxe.maxe_build_permutation(args.seed + m, A.cols, 1)
+        r = maxe.maxe_build_permutation(seed + m, A.rows, 0)
+        c = maxe.maxe_build_permutation(seed + m, A.cols, 1)
         h = maxe.from_csr(A, r, c)
-        if not (args.profile or args.no_tune):
+        if tune:
             maxe.maxe_batch_tune(h, k)
         hs.append(h)
         kp = 1 if k == 1 else (k + 3) // 4 * 4  # 16-byte rows for k > 1; unit strides for SpMV
@@ -451,77 +495,94 @@ def run_batched(args):
         for h, X, Y in zip(hs, Xs, Yp):
             maxe.maxe_spmm(h, X, Y, permuted=True)
 
-    if args.profile:
+    if profile:
         for _ in range(3):
             step_batched()
         torch.cuda.synchronize()
-        print(json.dumps({"profile": "done", "matrices": len(mats)}))
-        return
-
-    K = max(1, args.steps // 100)
-    clocks = Clocks(local)
-    clocks.start()
-    ms_b = timed_steps(step_batched, K * 10, args.warmup, world, graph_len=10)
-    clk = clocks.stop()
-    ms_pm_graph = timed_steps(step_permatrix, K, args.warmup, world, graph_len=1 if K < 2 else 2)
-    ms_pm = timed_steps(step_permatrix, K, args.warmup, world, graph_len=1)
+        return None
+    K = max(1, steps)
+    ms_b, g_b = timed_steps(step_batched, K * 10, warmup, world, graph_len=10)
+    ms_pm_graph, _ = timed_steps(step_permatrix, K, warmup, world, graph_len=1 if K < 2 else 2)
+    ms_pm, _ = timed_steps(step_permatrix, K, warmup, world, graph_len=1)
+    same = all(torch.equal(y1, y2) for y1, y2 in zip(Ys, Yp))  # one batch item = its own launch, bit for bit
     plans = [maxe.maxe_batch_plan_info(h) for h in hs]
     hbm, src = peaks()
     gbs = total / (ms_b * 1e-3) / 1e9
-    out = {
-        "metric": "batched SpMV/SpMM GB/s (config: 256 uneven matrices, 1-16 RHS), one persistent launch vs "
-                  "per-matrix launches", "value": round(gbs * world, 3), "unit": "GB/s", "n_gpus": world,
-        "ms_per_batch": ms_b, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    b.close()
+    for h in hs:
+        h.close()
+    return {
+        "value": round(gbs * world, 3), "unit": "GB/s", "ms_per_batch": ms_b,
         "config": {"workload": "256 square matrices, rows log-uniform 1k-200k, Poisson(U[8,64]) row lengths, "
                                "uniform distinct columns, FP32, k ~ U{1..16}, R-C permuted, vectors permuted",
                    "matrices": len(mats), "total_nnz": int(sum(A.nnz for A in mats)),
-                   "rows_total": int(sum(A.rows for A in mats)), "alg_bytes_per_batch": total},
+                   "rows_total": int(sum(A.rows for A in mats)), "alg_bytes_per_batch": total,
+                   "timing": f"{K * 10} batches{' (CUDA graph of 10)' if g_b else ''}; per-matrix: {K} batches"},
         "per_matrix_launches": {"ms_per_batch_stream": ms_pm, "ms_per_batch_graph": ms_pm_graph,
                                 "gbs_stream": round(total / (ms_pm * 1e-3) / 1e9, 3),
                                 "gbs_graph": round(total / (ms_pm_graph * 1e-3) / 1e9, 3)},
-        "speedup_vs_per_matrix_stream": round(ms_pm / ms_b, 3),
-        "speedup_vs_per_matrix_graph": round(ms_pm_graph / ms_b, 3),
+        "over_per_matrix": round(ms_pm_graph / ms_b, 3),
+        "over_per_matrix_stream": round(ms_pm / ms_b, 3),
+        "items_equal_to_single_launches": bool(same),
         "roofline": {"bound": "hbm", "achieved": round(gbs, 3), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "peak_source": src},
         "plans": {"entries_per_task": sorted({p[0] for p in plans})[:8],
-                  "items16": sum(1 for p in plans if p[2] == 16)},
-        "gen_s": t_gen, "prep_and_tune_s": t_prep, "clocks": clk,
-        "gpu_launches_per_batch": 1,
+                  "items16": sum(1 for p in plans if p[2] == 16), "tuned": bool(tune)},
+        "gen_s": t_gen, "prep_and_tune_s": t_prep, "gpu_launches_per_batch": 1,
     }
+
+
+def run_batched(args):
+    from paper_2308_00106_gb300 import maxe
+
+    rank, world, local = dist_setup(args)
+    maxe.load(build_if_missing=(rank == 0))
+    clocks = Clocks(local)
+    clocks.start()
+    out = batched_measure(args.seed, args.batch_count, max(1, args.steps // 100), args.warmup, world,
+                          tune=not (args.profile or args.no_tune), profile=args.profile)
+    clk = clocks.stop()
+    if out is None:
+        print(json.dumps({"profile": "done"}))
+        return
+    out = {"metric": "batched SpMV/SpMM GB/s (config: 256 uneven matrices, 1-16 RHS), one persistent launch vs "
+                     "per-matrix launches", "n_gpus": world, "higher_is_better": True, "dtype": "f32",
+           "data": "synthetic", **out, "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
 
 
-def run_serving(args):
+def serving_measure(seed, requests, loads=(0.5, 0.8, 0.95), unbatched=True):
     """64 resident permuted matrices, Poisson request stream (60% SpMV, 30% SpMM
-    k = 2..32, 10% 20-step power iteration), 60 GB device-memory cap."""
+    k = 2..32, 10% 20-step power iteration), 60 GB device-memory cap: saturation
+    throughput, p50/p99 latency at fractions of it, the same server without
+    batching, and the same requests launched back to back with no scheduler."""
     from paper_2308_00106_gb300 import maxe, serve
     from paper_2308_00106_gb300 import workloads as W
 
-    rank, world, local = dist_setup(args)
-    maxe.load(build_if_missing=(rank == 0))
     t0 = time.perf_counter()
-    mats = W.serving_set(args.seed, device="cuda")
+    mats = W.serving_set(seed, device="cuda")
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    srv = serve.Server(mats, seed=args.seed, mem_cap_bytes=60 << 30)
+    srv = serve.Server(mats, seed=seed, mem_cap_bytes=60 << 30)
     t_load = time.perf_counter() - t0
-    n = args.requests
+    n = requests
     # warm-up, then saturation: every request queued at t = 0
-    srv.run(serve.make_trace(200, len(mats), math.inf, seed=1))
-    clocks = Clocks(local)
-    clocks.start()
+    srv.run(serve.make_trace(min(200, n), len(mats), math.inf, seed=1))
     sat = srv.run(serve.make_trace(n, len(mats), math.inf, seed=2))
-    loads = {}
-    for f in (0.5, 0.8, 0.95):
-        loads[str(f)] = srv.run(serve.make_trace(n, len(mats), f * sat["req_per_s"], seed=3 + int(f * 100)))
-    clk = clocks.stop()
-    # the same server without batching (one request per step), same traces
-    unb_sat = srv.run(serve.make_trace(n, len(mats), math.inf, seed=2), max_items=1)
-    unb_loads = {}
-    for f in (0.5, 0.8):
-        unb_loads[str(f)] = srv.run(serve.make_trace(n, len(mats), f * sat["req_per_s"], seed=3 + int(f * 100)),
-                                    max_items=1)
+    at = {}
+    for f in loads:
+        at[str(f)] = srv.run(serve.make_trace(n, len(mats), f * sat["req_per_s"], seed=3 + int(f * 100)))
+    unb = None
+    if unbatched:
+        unb_sat = srv.run(serve.make_trace(n, len(mats), math.inf, seed=2), max_items=1)
+        unb_loads = {}
+        for f in loads[:2]:
+            unb_loads[str(f)] = srv.run(serve.make_trace(n, len(mats), f * sat["req_per_s"], seed=3 + int(f * 100)),
+                                        max_items=1)
+        unb = {"saturation": {k: unb_sat[k] for k in ("req_per_s", "gbs", "p50_ms", "p99_ms")},
+               "loads": {f: {k: v[k] for k in ("req_per_s", "gbs", "p50_ms", "p99_ms")} for f, v in unb_loads.items()},
+               "throughput_over": round(sat["req_per_s"] / unb_sat["req_per_s"], 3)}
     # the same saturation trace served one request at a time with single-matrix launches
     trace = serve.make_trace(n, len(mats), math.inf, seed=2)
     torch.cuda.synchronize()
@@ -549,28 +610,41 @@ def run_serving(args):
     t_seq = time.perf_counter() - t0
     hbm, src = peaks()
     out = {
-        "metric": "served p50/p99 latency and GB/s (config: 64 resident permuted matrices, Poisson SpMV/SpMM/"
-                  "power-iteration stream, 60 GB cap)", "value": round(sat["gbs"], 3), "unit": "GB/s",
-        "n_gpus": world, "higher_is_better": True, "dtype": "f32/bf16 values, f32 vectors", "data": "synthetic",
+        "value": round(sat["gbs"], 3), "unit": "GB/s",
         "config": {"workload": "64 square matrices, rows log-uniform 10k-4M, Poisson(U[5,50]) row lengths, half "
                                "FP32 half BF16 values, R-C permuted; requests 60% SpMV, 30% SpMM k~U{2..32}, 10% "
                                "20-step power iteration; device-memory admission cap 60 GB",
                    "requests_per_trace": n, "resident_bytes": srv.resident_bytes,
                    "total_nnz": int(sum(A.nnz for A in mats))},
-        "saturation": sat, "loads": loads,
-        "unbatched_server": {"saturation": {k: unb_sat[k] for k in ("req_per_s", "gbs", "p50_ms", "p99_ms")},
-                             "loads": {f: {k: v[k] for k in ("req_per_s", "gbs", "p50_ms", "p99_ms")}
-                                       for f, v in unb_loads.items()}},
-        "throughput_vs_unbatched_server": round(sat["req_per_s"] / unb_sat["req_per_s"], 3),
+        "saturation": sat, "loads": at,
+        "p50_ms": {f: round(v["p50_ms"], 3) for f, v in at.items()},
+        "p99_ms": {f: round(v["p99_ms"], 3) for f, v in at.items()},
         "one_request_at_a_time_bare_launches": {"req_per_s": n / t_seq, "gbs": bytes_seq / t_seq / 1e9,
                                                 "what": "requests launched back to back with no scheduler, "
                                                         "no arrivals and no latency accounting"},
-        "throughput_vs_bare_launches": round(sat["req_per_s"] / (n / t_seq), 3),
+        "over_bare": round(sat["req_per_s"] / (n / t_seq), 3),
         "roofline": {"bound": "hbm", "achieved": round(sat["gbs"], 3), "peak": hbm, "unit": "GB/s",
                      "frac": round(sat["gbs"] / hbm, 4), "peak_source": src},
-        "gen_s": t_gen, "load_and_tune_s": t_load, "clocks": clk,
+        "gen_s": t_gen, "load_and_tune_s": t_load,
     }
+    if unb is not None:
+        out["unbatched_server"] = unb
     srv.close()
+    return out
+
+
+def run_serving(args):
+    from paper_2308_00106_gb300 import maxe
+
+    rank, world, local = dist_setup(args)
+    maxe.load(build_if_missing=(rank == 0))
+    clocks = Clocks(local)
+    clocks.start()
+    out = serving_measure(args.seed, args.requests)
+    clk = clocks.stop()
+    out = {"metric": "served p50/p99 latency and GB/s (config: 64 resident permuted matrices, Poisson SpMV/SpMM/"
+                     "power-iteration stream, 60 GB cap)", "n_gpus": world, "higher_is_better": True,
+           "dtype": "f32/bf16 values, f32 vectors", "data": "synthetic", **out, "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
 
@@ -620,7 +694,7 @@ def run_laplacian_table(args):
                     step = lambda: maxe.maxe_spmv(h, x1, y1, permuted=True)  # noqa: E731
                 else:
                     step = lambda: maxe.maxe_spmm(h, X, Y, permuted=True)  # noqa: E731
-                ms = timed_steps(step, K, 3, world, graph_len=5)
+                ms, _ = timed_steps(step, K, 3, world, graph_len=5)
                 by = alg_bytes(M, N, A.nnz, vb, xb, xb, k)
                 gbs = by / (ms * 1e-3) / 1e9
                 rows_out.append({"dtype": dtype, "order": order, "k": k, "ms": round(ms, 4), "gbs": round(gbs, 1),
@@ -670,7 +744,7 @@ def run_partition_table(args):
                     step = lambda: maxe.maxe_coo_spmv(h, xp, y, permuted=True)  # noqa: E731
                 else:
                     step = lambda: maxe.maxe_spmv(h, xp, y, permuted=True)  # noqa: E731
-                ms = timed_steps(step, K, 3, world, graph_len=10)
+                ms, _ = timed_steps(step, K, 3, world, graph_len=10)
                 gbs = alg_bytes(M, N, A.nnz, 4, 4, 4) / (ms * 1e-3) / 1e9  # CSR bytes: COO reads 4 more per entry
                 rows_out.append({"matrix": wname, "order": order, "partition": part, "ms": round(ms, 4),
                                  "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)})
@@ -731,7 +805,7 @@ def run_shuffle_table(args):
             for part, hh in handles.items():
                 y = torch.empty(M, device="cuda")
                 step = lambda: maxe.maxe_spmv(hh, xp, y, permuted=True)  # noqa: E731
-                ms = timed_steps(step, K, 3, world, graph_len=10)
+                ms, _ = timed_steps(step, K, 3, world, graph_len=10)
                 gbs = alg_bytes(M, N, A.nnz, 4, 4, 4) / (ms * 1e-3) / 1e9
                 row[part] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)}
                 hh.close()
@@ -744,6 +818,40 @@ def run_shuffle_table(args):
            "table": rows_out, "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
+
+
+def by_dtype_measure(base, rperm, cperm, K, warmup, world, dtypes=("f64", "bf16")):
+    """The headline matrix with its values stored in other types (a8): the same
+    launch configuration (autotuned handles, vectors in the permuted space),
+    permuted and natural order.  Returns {dtype: {order: record}} and, per
+    (dtype, order), the original-space product y = A x of the same handle for
+    the oracle check (the same kernel and values, x gathered and y scattered)."""
+    from paper_2308_00106_gb300 import maxe
+    from paper_2308_00106_gb300 import workloads as W
+
+    hbm, _ = peaks()
+    M, N, Z = base.rows, base.cols, base.nnz
+    out, ys = {}, {}
+    for dt in dtypes:
+        A = base.astype(dt)
+        vb = {"f64": 8, "f32": 4, "bf16": 2}[dt]
+        xb = 8 if dt == "f64" else 4
+        by = alg_bytes(M, N, Z, vb, xb, xb)
+        x = W.vector(1, N, "f64" if dt == "f64" else "f32", "cuda")
+        out[dt] = {}
+        for order, perms in (("permuted", (rperm, cperm)), ("plain", (None, None))):
+            h = maxe.from_csr(A, *perms, autotune=True)
+            xp = maxe.maxe_permute_gather(cperm, x) if order == "permuted" else x
+            y = torch.empty(M, dtype=x.dtype, device="cuda")
+            ms, _ = timed_steps(lambda: maxe.maxe_spmv(h, xp, y, permuted=True), K, warmup, world, 50)
+            gbs = by / (ms * 1e-3) / 1e9
+            out[dt][order] = {"gbs": round(gbs, 1), "frac": round(gbs / hbm, 4), "us": round(ms * 1e3, 2),
+                              "alg_bytes": by, "kernel": ("x-sliced" + (" pairs" if h.xslice_pairs() else ""))
+                              if h.xslice() else "csr"}
+            ys[(dt, order)] = maxe.maxe_spmv(h, x).cpu().numpy()
+            h.close()
+        del A
+    return out, ys
 
 
 def main():
@@ -772,7 +880,16 @@ def main():
     ap.add_argument("--seeds", type=int, default=32, help="permutation seeds of the min/mean/max sweep (0: skip)")
     ap.add_argument("--profile", action="store_true",
                     help="no timing: 3 permuted then 3 plain SpMV launches (for an ncu capture)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: leave out the by-value-type, serving and batched sections")
+    ap.add_argument("--serve-requests", type=int, default=400, help="requests per trace of the serving section")
+    ap.add_argument("--record-profile", nargs=4, metavar=("CSV", "KERNEL", "LAUNCH", "COMMAND"),
+                    help="write profiles/<record>.json from an ncu raw CSV export (no GPU needed)")
     args = ap.parse_args()
+    if args.record_profile:
+        csv_path, kernel, launch, command = args.record_profile
+        print(json.dumps(record_profile(csv_path, kernel, int(launch), command, args.workload)))
+        return
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -842,10 +959,10 @@ def main():
 
     clocks = Clocks(local)
     clocks.start()
-    ms_perm = timed_steps(step_perm, args.steps, args.warmup, world, args.graph_len)
+    ms_perm, graphed = timed_steps(step_perm, args.steps, args.warmup, world, args.graph_len)
     clk = clocks.stop()
-    ms_plain = timed_steps(step_plain, args.steps, args.warmup, world, args.graph_len)
-    ms_full = timed_steps(step_full, max(args.steps // 4, 1), args.warmup, world, args.graph_len)
+    ms_plain, _ = timed_steps(step_plain, args.steps, args.warmup, world, args.graph_len)
+    ms_full, _ = timed_steps(step_full, max(args.steps // 4, 1), args.warmup, world, args.graph_len)
     fl_perm = flushed_launch_ms(step_perm, reps=200)
     fl_plain = flushed_launch_ms(step_plain, reps=200)
     seeds = seed_sweep(A, x, args, world, tune) if args.seeds > 0 else None
@@ -880,9 +997,24 @@ def main():
         raise SystemExit("end-to-end result differs from the timed device result")
 
     kern = "spmv_xslice_kernel" if hP.xslice() else "spmm_warp_kernel"
-    traffic, rev = traffic_from_profile(PROFILE_OF[kern])
-    if rev != KERNEL_REVISION[kern]:
-        traffic = None
+    traffic = traffic_from_record(kern)
+
+    # ---- the rest of the metric: other value types, the served and batched forms
+    by_dtype, by_dtype_y, serving, batched = None, {}, None, None
+    if not args.no_extras and args.workload == "powerlaw":
+        K_x = max(min(args.steps, 2000), 2)
+        by_dtype, by_dtype_y = by_dtype_measure(A, rperm, cperm, K_x, args.warmup, world)
+        by_dtype["f32"] = {"permuted": {"gbs": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                                        "us": round(ms_perm * 1e3, 2), "alg_bytes": bytes_step,
+                                        "kernel": ("x-sliced" + (" pairs" if hP.xslice_pairs() else ""))
+                                        if hP.xslice() else "csr"},
+                           "plain": {"gbs": round(gbs_plain, 1), "frac": round(gbs_plain / hbm, 4),
+                                     "us": round(ms_plain * 1e3, 2), "alg_bytes": bytes_step,
+                                     "kernel": "x-sliced" if hN.xslice() else "csr"}}
+        by_dtype_y[("f32", "permuted")] = maxe.maxe_spmv(hP, x).cpu().numpy()
+        by_dtype_y[("f32", "plain")] = maxe.maxe_spmv(hN, x).cpu().numpy()
+        serving = serving_measure(args.seed, args.serve_requests, loads=(0.5, 0.8), unbatched=False)
+        batched = batched_measure(args.seed, 256, max(1, min(args.steps // 10, 5)), args.warmup, world, tune=True)
 
     out = {
         "metric": METRIC, "value": round(job_rate(bytes_step, ms_perm, world) / 1e9, 3), "unit": "GB/s",
@@ -893,7 +1025,9 @@ def main():
                    "variant": "permuted R-C (rows and columns), vectors in permuted space",
                    "l2": "inputs larger than L2 (matrix %.0f MB > 129 MB); x', y' stay L2-resident across steps"
                          % (bytes_step / 1e6),
-                   "timing": f"CUDA graph of {args.graph_len} steps replayed, CUDA events, max over ranks",
+                   "timing": (f"{args.steps} steps as CUDA graph replays of {min(args.graph_len, args.steps)} "
+                              f"steps" if graphed else f"{args.steps} eager launch(es)")
+                             + ", CUDA events on the launching stream, max over ranks",
                    "parallelism": "replicas only" if world > 1 else "single GPU"},
         "plain": {"value": round(gbs_plain * world, 3), "unit": "GB/s", "ms_per_step": ms_plain,
                   "frac": round(gbs_plain / hbm, 4)},
@@ -920,6 +1054,9 @@ def main():
                         "steps alternate over two streams"},
         "gpu_launches": args.steps,
         "clocks": clk,
+        **({"by_dtype": by_dtype} if by_dtype else {}),
+        **({"serving": serving} if serving else {}),
+        **({"batched": batched} if batched else {}),
         "context": "paper: ~15% gain from randomization on AMD GPU-CPU systems (FP64, rocSPARSE); context only",
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -932,6 +1069,21 @@ def main():
                                "host": host_info(),
                                "rel_l2_gpu_vs_oracle": float(np.linalg.norm(got - y_cpu) /
                                                              max(np.linalg.norm(y_cpu), 1e-300))}
+        if by_dtype:
+            # every value type and order against the FP64 oracle on its stored
+            # values, all rows (y = A x through each handle, original space)
+            import oracle
+            rp0, co0 = A.rowptr.cpu().numpy(), A.col.cpu().numpy()
+            x64 = x.cpu().double().numpy()
+            for dt in by_dtype:
+                vv = A.astype(dt).val.cpu()
+                vv = vv.view(torch.int16).numpy().view(np.uint16) if dt == "bf16" else vv.numpy()
+                xd = W.vector(1, N, "f64" if dt == "f64" else "f32", "cpu").double().numpy() if dt == "f64" else x64
+                ref = oracle.spmv(M, rp0, co0, vv, W.DTYPE_CODE[dt], xd)
+                for order in by_dtype[dt]:
+                    yy = by_dtype_y[(dt, order)].astype(np.float64)
+                    by_dtype[dt][order]["rel_l2_vs_oracle"] = float(np.linalg.norm(yy - ref) /
+                                                                    max(np.linalg.norm(ref), 1e-300))
     if rank == 0:
         print(json.dumps(out))
     hP.close()

@@ -87,17 +87,26 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * 17, else 9) per 256 entries. */
 #define MAXE_COO 0x40u
 /* Flag of maxe_permute_csr: also build the x-sliced form of A' and use it for
- * SpMV (k = 1, 16-byte aligned x).  The columns are cut into 64 KB slices of x
- * (16384 FP32 / 8192 FP64 columns), the rows into one tile per SM; each tile's
- * warps own row ranges and read their entries slice by slice, gathering x from
- * shared memory instead of L2 (one L2 request per nonzero on a randomly
- * permuted matrix is what bounds the CSR kernel there).  Costs 4 + value-size
- * bytes per entry more memory (each (row range, slice) cell padded to 32
- * entries, plus 12 bytes of descriptor per cell) and a synchronising build.
+ * SpMV (k = 1, 16-byte aligned x).  The columns are cut into slices of x that
+ * fit in shared memory (64 KB: 16384 FP32 / 8192 FP64 columns; 48 KB with
+ * column halves), the rows into one tile per SM; each tile's warps own row
+ * ranges and read their entries slice by slice, gathering x from shared memory
+ * instead of L2 (one L2 request per nonzero on a randomly permuted matrix is
+ * what bounds the CSR kernel there).  When the nonzeros of every tile split
+ * evenly between the two halves of the columns (FP32 and BF16 values), a tile
+ * runs on a cluster of two CTAs, one per half, whose sums are added in a fixed
+ * order.  Costs 4 + value-size bytes per entry more memory (plus 12 bytes of
+ * descriptor per (row range, slice) cell) and a synchronising build.
  * MAXE_AUTOTUNE builds it too when its x traffic would stay under four times
  * the matrix, and keeps it only if it times faster than the CSR kernel.
  * Ignored with MAXE_EQUAL_ROWS.  Deterministic. */
 #define MAXE_XSLICE 0x80u
+/* Tuning overrides of the x-sliced form (with MAXE_XSLICE or MAXE_AUTOTUNE):
+ * MAXE_XS_PAIRS runs every tile on a cluster of two CTAs, one per half of the
+ * columns, even when the halves are uneven (FP32 and BF16 values; FP64 values
+ * never use pairs); MAXE_XS_SINGLE never does.  Not both. */
+#define MAXE_XS_PAIRS 0x100u
+#define MAXE_XS_SINGLE 0x200u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -182,7 +191,7 @@ MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_
  * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
  * (the "plain" matrix).  The handle keeps its own copies of the permutations.
  * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16, MAXE_SPMM_LANES,
- * MAXE_EQUAL_ROWS, MAXE_COO, MAXE_XSLICE.  *out receives the new handle.
+ * MAXE_EQUAL_ROWS, MAXE_COO, MAXE_XSLICE, MAXE_XS_PAIRS, MAXE_XS_SINGLE.  *out receives the new handle.
  * Synchronises `stream` once (to size the pass over rows longer than 2048).
  * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
 MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
@@ -199,7 +208,8 @@ MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, c
  * MAXE_SPMM_LANES at creation: *items = entries per lane of the SpMV variant
  * (8 or 16), plus 0x100 when SpMM uses columns across lanes, plus 0x200 when
  * SpMV uses the x-sliced form (MAXE_XSLICE), plus 0x400 when that form's cells
- * are large enough for its L2 prefetch cursor.  items: (host). */
+ * are large enough for its L2 prefetch cursor, plus 0x800 when it runs its tiles
+ * on pairs of CTAs (column halves).  items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;
@@ -235,7 +245,9 @@ MAXE_API maxe_status maxe_entropy_levels(const int64_t* counts_dev, int32_t gr, 
  *   - gr * gc must be <= 65536; larger grids return MAXE_ERR_INVALID.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before any
- *     stream capture.
+ *     stream capture.  The address belongs to the device's context: a call
+ *     after the context was destroyed and made anew (cudaDeviceReset) looks
+ *     it up again.
  *   - Every call on a device shares the one array and leaves its counts in
  *     it; each call clears the cells it uses before counting.  Calls that
  *     overlap on the GPU (other streams, other host threads) race on the array
@@ -332,6 +344,15 @@ MAXE_API maxe_status maxe_batch_plan_info(const maxe_handle* h, int64_t* entries
 MAXE_API maxe_status maxe_power_iteration(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
                                  double* lambda_host, void* stream);
 
+/* maxe_power_iteration that also returns, in lambda_hist_host[s] (host,
+ * `steps` doubles), the Rayleigh quotient v_s^T A v_s of the iterate after
+ * step s + 1 (the last one equals lambda), taken from the product that starts
+ * the next step: no extra products.  Same arguments and errors otherwise
+ * (INVALID when lambda_hist_host is NULL). */
+MAXE_API maxe_status maxe_power_iteration_history(const maxe_handle* h, const void* v0, int32_t steps,
+                                                  void* v_out, double* lambda_host, double* lambda_hist_host,
+                                                  void* stream);
+
 /* Vector steps of a batched power iteration kept in the permuted space (used
  * by the serving loop; not in the paper).  With Q = rinv[cperm] (so that
  * u_next = P_c^{-1} P_r^{-1} w for w = A' u), square matrices only:
@@ -355,6 +376,21 @@ MAXE_API maxe_status maxe_handle_destroy(maxe_handle* h);
  * MAXE_ERR_TIMEOUT if a bounded wait ran out since the last call, else MAXE_OK
  * (or MAXE_ERR_CUDA if the stream reported an error). */
 MAXE_API maxe_status maxe_device_status(void* stream);
+
+/* Time after which every bounded device-side wait of the library's kernels on
+ * the current device gives up (the kernel then records MAXE_ERR_TIMEOUT, stops
+ * its work and returns, leaving the context usable).  ns = 0 restores the
+ * default of 2 s; at most 60 s (MAXE_ERR_INVALID above).  The limit is a
+ * parameter of each launch: it affects kernels launched after the call, and a
+ * CUDA graph keeps the limit its kernels were captured with. */
+MAXE_API maxe_status maxe_set_wait_limit_ns(uint64_t ns);
+
+/* Self-test of the timeout path: launches on `stream` one small kernel that
+ * waits on an mbarrier nothing completes.  Its bounded wait runs out after the
+ * wait limit, records the timeout and the kernel returns; the next
+ * maxe_device_status(stream) reports MAXE_ERR_TIMEOUT.  Occupies one SM for
+ * the wait limit: lower the limit first (maxe_set_wait_limit_ns). */
+MAXE_API maxe_status maxe_selftest_wait(void* stream);
 
 /* Human-readable name of a status code. */
 MAXE_API const char* maxe_status_str(maxe_status s);

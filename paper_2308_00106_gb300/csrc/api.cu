@@ -1,12 +1,32 @@
 // api.cu -- the extern "C" entry points of libmaxe.so (declared in include/maxe.h).
 // Host-side argument checks, handle lifetime, and dispatch to the kernel
 // families; no arithmetic of the method runs here.
+#include <atomic>
 #include <mutex>
 #include <new>
 
 #include "handle.cuh"
 
 namespace maxe {
+
+namespace {
+std::atomic<uint64_t> g_wait_ns[64];  // 0: kWaitNs
+}  // namespace
+
+uint64_t wait_limit_ns(int device) {
+  if (device < 0 || device >= 64) return kWaitNs;
+  const uint64_t v = g_wait_ns[device].load(std::memory_order_relaxed);
+  return v ? v : kWaitNs;
+}
+
+uint64_t wait_limit_ns() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return kWaitNs;
+  }
+  return wait_limit_ns(dev);
+}
 
 maxe_status device_info(DeviceInfo* out) {
   static std::mutex mu;
@@ -20,14 +40,30 @@ maxe_status device_info(DeviceInfo* out) {
     DeviceInfo d{};
     d.device = dev;
     MAXE_CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-    MAXE_CUDA_TRY(cudaMalloc(&d.status, sizeof(unsigned)));
-    MAXE_CUDA_TRY(cudaMemset(d.status, 0, sizeof(unsigned)));
+    MAXE_CUDA_TRY(cudaMalloc(&d.status, kDevWordBytes));
+    MAXE_CUDA_TRY(cudaMemset(d.status, 0, kDevWordBytes));
     infos[dev] = d;
     ready[dev] = true;
   }
   *out = infos[dev];
   return MAXE_OK;
 }
+
+namespace {
+
+// A wait on an mbarrier that nothing completes: it runs out after the wait
+// limit, records the timeout and returns (the test of the failure path).
+__global__ void selftest_wait_kernel(unsigned* status, uint64_t lim) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, status, lim);
+}
+
+}  // namespace
 
 }  // namespace maxe
 
@@ -147,8 +183,9 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return MAXE_ERR_INVALID;
   if (A->nnz > 0 && (A->rows == 0 || A->cols == 0)) return MAXE_ERR_INVALID;
   if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16 | MAXE_SPMM_LANES |
-                                     MAXE_EQUAL_ROWS | MAXE_COO | MAXE_XSLICE))
+                                     MAXE_EQUAL_ROWS | MAXE_COO | MAXE_XSLICE | MAXE_XS_PAIRS | MAXE_XS_SINGLE))
     return MAXE_ERR_INVALID;
+  if ((flags & MAXE_XS_PAIRS) && (flags & MAXE_XS_SINGLE)) return MAXE_ERR_INVALID;
   DeviceInfo di{};
   MAXE_TRY(device_info(&di));
   cudaStream_t st = as_stream(stream);
@@ -167,7 +204,8 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (s == MAXE_OK) s = ensure_xbuf(h, 1, st);
   if (s == MAXE_OK && (flags & MAXE_COO)) s = coo_build(h, st);
   if (s == MAXE_OK && (flags & (MAXE_XSLICE | MAXE_AUTOTUNE)) && !h->equal_rows) {
-    s = xslice_build(h, st, (flags & MAXE_XSLICE) != 0);
+    const int pairs = (flags & MAXE_XS_PAIRS) ? 1 : ((flags & MAXE_XS_SINGLE) ? -1 : 0);
+    s = xslice_build(h, st, (flags & MAXE_XSLICE) != 0, pairs);
     // only the autotuner asked for it: without the memory, the handle goes without it
     if (s == MAXE_ERR_OOM && !(flags & MAXE_XSLICE)) {
       xslice_release(h);
@@ -204,7 +242,7 @@ maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view, const int32_t*
 maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
   if (!h || !items) return MAXE_ERR_INVALID;
   *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0) | (h->xs_use ? 0x200 : 0) |
-           (h->xs_use && h->xs_prefetch ? 0x400 : 0);
+           (h->xs_use && h->xs_prefetch ? 0x400 : 0) | (h->xs_use && h->xs_pair == 2 ? 0x800 : 0);
   return MAXE_OK;
 }
 
@@ -273,11 +311,34 @@ maxe_status maxe_power_iteration(const maxe_handle* h, const void* v0, int32_t s
                                  double* lambda_host, void* stream) {
   if (!h || !lambda_host || steps < 0 || h->rows != h->cols) return MAXE_ERR_INVALID;
   if (h->rows > 0 && (!v0 || !v_out)) return MAXE_ERR_INVALID;
-  return power_iteration_run(h, v0, steps, v_out, lambda_host, as_stream(stream));
+  return power_iteration_run(h, v0, steps, v_out, lambda_host, nullptr, as_stream(stream));
+}
+
+maxe_status maxe_power_iteration_history(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
+                                         double* lambda_host, double* lambda_hist_host, void* stream) {
+  if (!h || !lambda_host || !lambda_hist_host || steps < 0 || h->rows != h->cols) return MAXE_ERR_INVALID;
+  if (h->rows > 0 && (!v0 || !v_out)) return MAXE_ERR_INVALID;
+  return power_iteration_run(h, v0, steps, v_out, lambda_host, lambda_hist_host, as_stream(stream));
 }
 
 maxe_status maxe_handle_destroy(maxe_handle* h) {
   release(h);
+  return MAXE_OK;
+}
+
+maxe_status maxe_set_wait_limit_ns(uint64_t ns) {
+  if (ns > 60000000000ull) return MAXE_ERR_INVALID;
+  DeviceInfo di{};
+  MAXE_TRY(device_info(&di));
+  g_wait_ns[di.device].store(ns, std::memory_order_relaxed);
+  return MAXE_OK;
+}
+
+maxe_status maxe_selftest_wait(void* stream) {
+  DeviceInfo di{};
+  MAXE_TRY(device_info(&di));
+  selftest_wait_kernel<<<1, 32, 0, as_stream(stream)>>>(di.status, wait_limit_ns(di.device));
+  MAXE_CUDA_TRY(cudaGetLastError());
   return MAXE_OK;
 }
 

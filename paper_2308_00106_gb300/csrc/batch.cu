@@ -47,6 +47,7 @@ struct BatchParams {
   unsigned* status;
   int32_t* next;         // dynamic task counter (zeroed before the launch)
   int32_t nitems, ntasks;
+  uint64_t wait_ns;      // limit of the bounded waits
 };
 
 // Kernel classes: register budgets differ a lot between the variants, so each
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(kThreads, BatchClass<VT, CLASS>::kMinBlocks) s
     p.yperm = it.yperm;
     p.wrow = it.wrow;
     p.status = bp.status;
+    p.wait_ns = bp.wait_ns;
     p.ldx = it.ldx;
     p.ldy = it.ldy;
     p.k = it.k;
@@ -131,16 +133,21 @@ int item_class(int vw, int unit, int it16) { return unit ? (it16 ? 1 : 0) : 2; }
 
 template <typename VT, int CLASS>
 maxe_status batch_prepare(int* blocks_per_sm) {
-  static int occ = -1;
-  if (occ < 0) {
+  static PerDeviceOnce once;  // the attribute and the occupancy are per device
+  static int occ[64] = {};
+  int dev = 0;
+  MAXE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return MAXE_ERR_UNSUPPORTED;
+  MAXE_TRY(once.run([dev] {
     const size_t smem = BatchClass<VT, CLASS>::warp_smem() * kWarps;
     MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_batch_kernel<VT, CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem)));
     int o = 0;
     MAXE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_batch_kernel<VT, CLASS>, kThreads, smem));
-    occ = o > 0 ? o : 1;
-  }
-  *blocks_per_sm = occ;
+    occ[dev] = o > 0 ? o : 1;
+    return MAXE_OK;
+  }));
+  *blocks_per_sm = occ[dev];
   return MAXE_OK;
 }
 
@@ -373,7 +380,7 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
     MAXE_CUDA_TRY(cudaMemcpyAsync(di, hi, sizeof(BatchItem) * m, cudaMemcpyHostToDevice, st));
     MAXE_CUDA_TRY(cudaMemcpyAsync(dt, ht, sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, st));
     MAXE_CUDA_TRY(cudaMemsetAsync(b->d_next + g, 0, sizeof(int32_t), st));
-    BatchParams bp{di, dt, b->status, b->d_next + g, m, static_cast<int32_t>(tasks)};
+    BatchParams bp{di, dt, b->status, b->d_next + g, m, static_cast<int32_t>(tasks), wait_limit_ns()};
     MAXE_TRY(launch_for(types[ti], cls, bp, b->sms, st));
   }
   if (cap == cudaStreamCaptureStatusNone) {

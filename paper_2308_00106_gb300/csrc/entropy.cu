@@ -208,22 +208,53 @@ constexpr int64_t kNoAllocMaxBins = 65536;  // grid cells the static scratch hol
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_entropy_scratch[kNoAllocMaxBins * sizeof(unsigned) + 256];
 
-// Device address of g_entropy_scratch, looked up once per device with that
-// device current (in host code the symbol is only a host-side stand-in).
+// The current context's id (driver calls resolved through the runtime, no
+// link to the driver library); 0 when it cannot be had.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_entropy_scratch, looked up on a device's first call with
+// that device current (in host code the symbol is only a host-side stand-in).
+// The address belongs to the device's context: a call after the context was
+// torn down and made again (cudaDeviceReset) looks it up again.
 maxe_status noalloc_scratch(unsigned char** out) {
   static std::mutex mu;
   static unsigned char* addr[64] = {};
+  static unsigned long long ctx_of[64] = {};
   int dev = 0;
   MAXE_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return MAXE_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!addr[dev] || (ctx != 0 && ctx != ctx_of[dev])) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_entropy_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return MAXE_ERR_CUDA;
     }
     addr[dev] = static_cast<unsigned char*>(p);
+    ctx_of[dev] = ctx != 0 ? ctx : current_context_id();  // the lookup made the context current if it was not
   }
   *out = addr[dev];
   return MAXE_OK;

@@ -35,17 +35,21 @@ struct maxe_handle {
   int64_t bH = 0;
   int bit16 = 0;                           // batch plan: 16 entries per lane for k = 1
   int blc = 0;                             // batch plan: SpMM with columns across lanes
-  // x-sliced SpMV form (MAXE_XSLICE): entries grouped by (warp range, column slice)
+  // x-sliced SpMV form (MAXE_XSLICE): entries grouped by ((tile, half, warp range), column slice)
   uint32_t* xs_idx = nullptr;              // (accumulator << 15) | column in slice, step-major cells
   void* xs_val = nullptr;
-  int32_t* xs_seg_start = nullptr;         // [G * nS], xs_seg_len and xs_seg_cut follow in the same block
-  int32_t* xs_seg_len = nullptr;
-  uint32_t* xs_seg_cut = nullptr;          // [G * nS] lane-boundary cuts of each cell
+  int32_t* xs_seg = nullptr;               // [3 * cells]: first entry, steps, full lanes | partial entries << 6
+  int64_t xs_cells = 0;
   int32_t* xs_tile_row = nullptr;          // [ntiles + 1]
-  int32_t* xs_warp_row = nullptr;          // [G + 1]
-  int32_t* xs_tl_off = nullptr;            // [ntiles + 1], xs_tl_slice follows in the same block
+  int32_t* xs_warp_row = nullptr;          // [ntiles * pair * 16], xs_vslot follows in the same block
+  int32_t* xs_vslot = nullptr;
+  int32_t* xs_vl_off = nullptr;            // [ntiles * pair * 15 + 1], xs_vl_item follows in the same block
+  int32_t* xs_vl_item = nullptr;
+  int32_t* xs_tl_off = nullptr;            // [ntiles * pair + 1], xs_tl_slice follows in the same block
   int32_t* xs_tl_slice = nullptr;
   int32_t xs_ntiles = 0, xs_nS = 0;
+  int32_t xs_pair = 1;                     // column halves per tile: 1, or 2 on a cluster of two CTAs
+  int32_t xs_smem = 0;                     // dynamic shared memory per CTA
   int64_t xs_bytes = 0;
   int xs_use = 0;                          // SpMV (k = 1) takes the x-sliced kernel
   int xs_prefetch = 0;                     // cells large enough for the L2 prefetch cursor
@@ -82,9 +86,10 @@ maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int
 maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st);
 
 // xslice.cu: build the x-sliced form (unless forced, leaves it unbuilt when it
-// would not pay);
-// launch y' = A' x' with it (x 16-byte aligned, unit strides); free it.
-maxe_status xslice_build(maxe_handle* h, cudaStream_t st, bool force);
+// would not pay; pairs: > 0 column halves on CTA pairs, 0 when the halves are
+// even, < 0 never); launch y' = A' x' with it (x 16-byte aligned, unit
+// strides); free it.
+maxe_status xslice_build(maxe_handle* h, cudaStream_t st, bool force, int pairs);
 bool xslice_ready(const maxe_handle* h, const void* x);
 maxe_status xslice_launch(const maxe_handle* h, const void* x, void* y, const int32_t* yperm, cudaStream_t st);
 void xslice_release(maxe_handle* h);
@@ -104,6 +109,6 @@ maxe_status permute_csr_run(const maxe_csr* A, const int32_t* rperm, const int32
 
 // power.cu
 maxe_status power_iteration_run(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
-                                double* lambda_host, cudaStream_t st);
+                                double* lambda_host, double* hist_host, cudaStream_t st);
 
 }  // namespace maxe

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/maxe.h"
 
 namespace maxe {
@@ -16,10 +18,11 @@ namespace maxe {
 constexpr int64_t kMaxIndex = 2147483647LL - 64;  // rows, cols, nnz bound
 constexpr int kPadElems = 4096;  // col/val arrays owned by a handle are rounded up to this multiple
 constexpr int kRowptrPad = 8;    // extra rowptr entries owned by a handle
-constexpr uint64_t kWaitNs = 2000000000ull;  // bounded device waits give up after 2 s
+constexpr uint64_t kWaitNs = 2000000000ull;  // bounded device waits give up after 2 s (default)
 
-// device status bits
+// The per-device status word every waiting kernel gets (DeviceInfo::status).
 constexpr unsigned kDevTimeout = 1u;
+constexpr size_t kDevWordBytes = 16;
 
 // ----------------------------------------------------------- device helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -65,15 +68,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; give up after kWaitNs,
-// record kDevTimeout in *status and return false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* status) {
+// Wait for the phase with the given parity to complete; give up after lim ns
+// (the launch's wait limit, a kernel parameter), record kDevTimeout in *status
+// and return false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* status, uint64_t lim) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
     for (int i = 0; i < 32; ++i)
       if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer_ns() - t0 > kWaitNs) {
+    if (global_timer_ns() - t0 > lim) {
       atomicOr(status, kDevTimeout);
       return false;
     }
@@ -136,6 +140,23 @@ __device__ __forceinline__ float bf16_bits_to_float(uint16_t b) {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Runs a set-up step (kernel attributes, which belong to a device's context)
+// once per device, under a lock: host threads may launch concurrently.
+struct PerDeviceOnce {
+  std::mutex mu;
+  bool done[64] = {};
+  template <typename F>
+  maxe_status run(F&& f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MAXE_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return MAXE_OK;
+    const maxe_status s = f();
+    if (s == MAXE_OK) done[dev] = true;
+    return s;
+  }
+};
+
 inline int64_t round_up(int64_t a, int64_t m) { return (a + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -143,9 +164,13 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 struct DeviceInfo {
   int device;
   int sms;
-  unsigned* status;  // device word, bits of kDev*
+  unsigned* status;  // device word (kDevWordBytes): bits of kDev*, then the wait limit
 };
 maxe_status device_info(DeviceInfo* out);
+// The wait limit (ns) of bounded device waits for kernels launched on `device`
+// (maxe_set_wait_limit_ns; kWaitNs by default).
+uint64_t wait_limit_ns(int device);
+uint64_t wait_limit_ns();  // the current device's
 
 // Scratch / owned allocations through a maxe_allocator (or cudaMallocAsync).
 struct Allocator {

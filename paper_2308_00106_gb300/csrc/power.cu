@@ -96,16 +96,21 @@ maxe_status dot(const T* a, const T* b, int64_t n, double* part, double* out, cu
   return MAXE_OK;
 }
 
+// hist_host (nullable): the Rayleigh quotient v^T A v of the iterate after
+// every step, taken from the product that starts the next step (no extra
+// products); the last one is lambda.
 template <typename T>
-maxe_status run(const maxe_handle* h, const T* v0, int32_t steps, T* v, double* lambda_host, cudaStream_t st) {
+maxe_status run(const maxe_handle* h, const T* v0, int32_t steps, T* v, double* lambda_host, double* hist_host,
+                cudaStream_t st) {
   const int64_t n = h->rows;
   ScratchSet scratch(h->al);
   T* w = scratch.get<T>(static_cast<size_t>(n));
   T* xp = scratch.get<T>(static_cast<size_t>(n));
-  double* part = scratch.get<double>(kDotBlocks + 2);
+  double* part = scratch.get<double>(kDotBlocks + 2 + (hist_host ? std::max(steps, 1) : 0));
   if (!w || !xp || !part) return MAXE_ERR_OOM;
   double* nrm2 = part + kDotBlocks;
   double* lam = part + kDotBlocks + 1;
+  double* hist = hist_host ? part + kDotBlocks + 2 : nullptr;
   MAXE_CUDA_TRY(cudaMemcpyAsync(v, v0, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
   const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, ceil_div(n, 256)));
   auto product = [&](const T* x, T* y) -> maxe_status {
@@ -118,6 +123,7 @@ maxe_status run(const maxe_handle* h, const T* v0, int32_t steps, T* v, double* 
   };
   for (int32_t s = 0; s < steps; ++s) {
     MAXE_TRY(product(v, w));
+    if (hist && s > 0) MAXE_TRY(dot(v, w, n, part, hist + s - 1, st));  // v = the iterate after step s
     MAXE_TRY(dot(w, w, n, part, nrm2, st));
     scale_by_inv_norm<T><<<grid, 256, 0, st>>>(w, nrm2, n, v);
     MAXE_CUDA_TRY(cudaGetLastError());
@@ -125,6 +131,11 @@ maxe_status run(const maxe_handle* h, const T* v0, int32_t steps, T* v, double* 
   MAXE_TRY(product(v, w));
   MAXE_TRY(dot(v, w, n, part, lam, st));
   MAXE_CUDA_TRY(cudaMemcpyAsync(lambda_host, lam, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (hist && steps > 0) {
+    if (steps > 1)
+      MAXE_CUDA_TRY(cudaMemcpyAsync(hist_host, hist, sizeof(double) * (steps - 1), cudaMemcpyDeviceToHost, st));
+    MAXE_CUDA_TRY(cudaMemcpyAsync(hist_host + steps - 1, lam, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
   MAXE_CUDA_TRY(cudaStreamSynchronize(st));
   return MAXE_OK;
 }
@@ -157,10 +168,11 @@ maxe_status dot_gather(const int32_t* Q, int64_t n, const T* u, const T* w, doub
 }  // namespace
 
 maxe_status power_iteration_run(const maxe_handle* h, const void* v0, int32_t steps, void* v_out,
-                                double* lambda_host, cudaStream_t st) {
+                                double* lambda_host, double* hist_host, cudaStream_t st) {
   if (h->dtype == MAXE_F64)
-    return run<double>(h, static_cast<const double*>(v0), steps, static_cast<double*>(v_out), lambda_host, st);
-  return run<float>(h, static_cast<const float*>(v0), steps, static_cast<float*>(v_out), lambda_host, st);
+    return run<double>(h, static_cast<const double*>(v0), steps, static_cast<double*>(v_out), lambda_host, hist_host,
+                       st);
+  return run<float>(h, static_cast<const float*>(v0), steps, static_cast<float*>(v_out), lambda_host, hist_host, st);
 }
 
 }  // namespace maxe

@@ -38,14 +38,13 @@ using namespace warp;
 
 template <typename VT, int VW, int IT, bool UNIT>
 maxe_status prepare_variant() {
-  static bool done = false;  // the attribute is per function and process
-  if (!done) {
+  static PerDeviceOnce once;  // the attribute is per function and device
+  return once.run([] {
     MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_warp_kernel<Cfg<VT, VW, IT, UNIT>>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(block_smem<VT, VW, IT>())));
-    done = true;
-  }
-  return MAXE_OK;
+    return MAXE_OK;
+  });
 }
 
 template <typename VT, int VW, int IT, bool UNIT>
@@ -59,13 +58,13 @@ maxe_status launch_variant(const Params& p, cudaStream_t st) {
 
 template <typename VT>
 maxe_status launch_lc(const Params& p, int g, cudaStream_t st) {
-  static bool done = false;
+  static PerDeviceOnce once;
   const size_t smem = sizeof(WarpSmemLC<VT>) * kWarps;
-  if (!done) {
+  MAXE_TRY(once.run([smem] {
     MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_lc_kernel<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem)));
-    done = true;
-  }
+    return MAXE_OK;
+  }));
   const unsigned grid = static_cast<unsigned>(ceil_div(p.nW, kWarps));
   spmm_lc_kernel<VT><<<grid, kThreads, smem, st>>>(p, g);
   MAXE_CUDA_TRY(cudaGetLastError());
@@ -158,6 +157,7 @@ maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t 
   p.Y = Y;
   p.yperm = yperm;
   p.status = h->status;
+  p.wait_ns = wait_limit_ns(h->device);
   p.ldx = ldx;
   p.ldy = ldy;
   p.k = k;

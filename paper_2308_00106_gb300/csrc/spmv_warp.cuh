@@ -42,6 +42,7 @@ struct Params {
   const int32_t* yperm;
   const int32_t* wrow;
   unsigned* status;
+  uint64_t wait_ns;  // limit of the bounded waits
   int64_t ldx, ldy;
   int32_t k, M, nW;
 };
@@ -302,7 +303,7 @@ __device__ __forceinline__ bool process_range(const Params& p, int32_t w, unsign
     const uint32_t fw = (ws.flags[(kItems * lane) >> 5] >> ((kItems * lane) & 31)) & ((1u << kItems) - 1u);
     const int first_flag = fw ? __ffs(fw) - 1 : kItems;
 
-    bool ok = mbar_wait_bounded(&ws.full[s], (g / kStages) & 1u, p.status);
+    bool ok = mbar_wait_bounded(&ws.full[s], (g / kStages) & 1u, p.status, p.wait_ns);
     if (!__all_sync(0xffffffffu, ok)) return false;
     int32_t cj[kItems];
     AT a[kItems];
@@ -546,7 +547,7 @@ __device__ __forceinline__ bool process_range_lc(const Params& p, int32_t w, uns
     const int e0 = q * C;  // the group's chunk, piece-relative
     const uint32_t wa = ws.flags[e0 >> 5];
     const uint32_t wb = ws.flags[min((e0 + C - 1) >> 5, kPiece / 32 - 1)];
-    bool ok = mbar_wait_bounded(&ws.full[s], (gg / kStages) & 1u, p.status);
+    bool ok = mbar_wait_bounded(&ws.full[s], (gg / kStages) & 1u, p.status, p.wait_ns);
     if (!__all_sync(0xffffffffu, ok)) return false;
     __syncwarp();
     if (lane < kPiece / 32) ws.flags[lane] = 0u;

@@ -15,6 +15,8 @@ import ctypes
 import os
 import threading
 
+import numpy as np
+
 import torch
 
 from . import build as _build
@@ -29,6 +31,8 @@ MAXE_SPMM_LANES = 0x10
 MAXE_EQUAL_ROWS = 0x20
 MAXE_COO = 0x40
 MAXE_XSLICE = 0x80
+MAXE_XS_PAIRS = 0x100
+MAXE_XS_SINGLE = 0x200
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -41,6 +45,7 @@ EXPORTS = [
     "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
     "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather", "maxe_entropy_levels",
     "maxe_nnz_histogram", "maxe_gradient_permutation", "maxe_coo_spmv", "maxe_handle_coo",
+    "maxe_power_iteration_history", "maxe_set_wait_limit_ns", "maxe_selftest_wait",
 ]
 MAXE_BATCH_SCATTER_Y = 0x1
 
@@ -120,8 +125,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_spmv": [P, P, P, U32, P],
             "maxe_spmm": [P, I32, P, I64, P, I64, U32, P],
             "maxe_power_iteration": [P, P, I32, P, ctypes.POINTER(ctypes.c_double), P],
+            "maxe_power_iteration_history": [P, P, I32, P, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), P],
             "maxe_handle_destroy": [P],
             "maxe_device_status": [P],
+            "maxe_set_wait_limit_ns": [ctypes.c_uint64],
+            "maxe_selftest_wait": [P],
             "maxe_batch_create": [I32, P, P, ctypes.POINTER(P)],
             "maxe_batch_set": [P, ctypes.POINTER(_BatchItem), I32],
             "maxe_batch_run": [P, P],
@@ -239,6 +248,10 @@ class Handle:
         """True when the x-sliced SpMV runs its L2 prefetch cursor (large cells)."""
         return bool(self._tuning() & 0x400)
 
+    def xslice_pairs(self) -> bool:
+        """True when the x-sliced SpMV runs each tile on a cluster of two CTAs (column halves)."""
+        return bool(self._tuning() & 0x800)
+
     def spmm_lanes(self) -> bool:
         """True when SpMM spreads the k columns across lanes (else column passes)."""
         return bool(self._tuning() & 0x100)
@@ -302,8 +315,11 @@ def maxe_permute_scatter(perm: torch.Tensor, y: torch.Tensor, stream=None):
 def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
                      stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False,
-                     equal_rows: bool = False, coo: bool = False, xslice: bool = False) -> Handle:
-    """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity."""
+                     equal_rows: bool = False, coo: bool = False, xslice: bool = False,
+                     xs_pairs: bool | None = None) -> Handle:
+    """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity.
+    xs_pairs: None lets the library decide whether the x-sliced form runs its
+    tiles on CTA pairs (column halves); True / False forces it on / off."""
     code = {torch.float64: MAXE_F64, torch.float32: MAXE_F32, torch.bfloat16: MAXE_BF16}[val.dtype]
     _dev(rowptr, torch.int32, "rowptr")
     _dev(col, torch.int32, "col")
@@ -317,7 +333,8 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
     out = ctypes.c_void_p()
     flags = ((MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
              | (MAXE_SPMM_LANES if spmm_lanes else 0) | (MAXE_EQUAL_ROWS if equal_rows else 0)
-             | (MAXE_COO if coo else 0) | (MAXE_XSLICE if xslice else 0))
+             | (MAXE_COO if coo else 0) | (MAXE_XSLICE if xslice else 0)
+             | (0 if xs_pairs is None else (MAXE_XS_PAIRS if xs_pairs else MAXE_XS_SINGLE)))
     _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
@@ -375,11 +392,18 @@ def maxe_spmm(h: Handle, X: torch.Tensor, Y: torch.Tensor | None = None, permute
     return Y
 
 
-def maxe_power_iteration(h: Handle, v0: torch.Tensor, steps: int, stream=None):
-    """(lambda, v) after `steps` normalised products in the original space."""
+def maxe_power_iteration(h: Handle, v0: torch.Tensor, steps: int, stream=None, history: bool = False):
+    """(lambda, v) after `steps` normalised products in the original space; with
+    history, (lambda, v, Rayleigh quotient after every step as a numpy array)."""
     _dev(v0, h.vec_dtype, "v0")
     v = torch.empty_like(v0)
     lam = ctypes.c_double()
+    if history:
+        hist = (ctypes.c_double * max(steps, 1))()
+        _check(load().maxe_power_iteration_history(ctypes.c_void_p(h.ptr), _ptr(v0), steps, _ptr(v),
+                                                   ctypes.byref(lam), hist, ctypes.c_void_p(_stream(stream))),
+               "maxe_power_iteration_history")
+        return lam.value, v, np.array(hist[:steps], dtype=np.float64)
     _check(load().maxe_power_iteration(ctypes.c_void_p(h.ptr), _ptr(v0), steps, _ptr(v), ctypes.byref(lam),
                                        ctypes.c_void_p(_stream(stream))), "maxe_power_iteration")
     return lam.value, v
@@ -389,15 +413,25 @@ def maxe_device_status(stream=None) -> int:
     return load().maxe_device_status(ctypes.c_void_p(_stream(stream)))
 
 
+def maxe_set_wait_limit_ns(ns: int):
+    """Bounded device waits give up after `ns` (0: the 2 s default)."""
+    _check(load().maxe_set_wait_limit_ns(ctypes.c_uint64(int(ns))), "maxe_set_wait_limit_ns")
+
+
+def maxe_selftest_wait(stream=None):
+    """Launch a wait on a flag nothing sets; it runs out after the wait limit."""
+    _check(load().maxe_selftest_wait(ctypes.c_void_p(_stream(stream))), "maxe_selftest_wait")
+
+
 def maxe_version() -> str:
     return load().maxe_version().decode()
 
 
 def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False,
-             spmm_lanes=False, equal_rows=False, coo=False, xslice=False) -> Handle:
+             spmm_lanes=False, equal_rows=False, coo=False, xslice=False, xs_pairs=None) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
     return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16,
-                            spmm_lanes, equal_rows, coo, xslice)
+                            spmm_lanes, equal_rows, coo, xslice, xs_pairs)
 
 
 class Batch:

@@ -71,3 +71,40 @@ def handle_arrays(h):
     else:
         v = v.numpy()
     return rp.cpu().numpy(), col.cpu().numpy(), v
+
+
+# unit roundoff of the accumulation: FP64 for FP64 values, FP32 otherwise
+UNIT = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "bf16": 2.0 ** -24}
+# BF16 values are decoded exactly and accumulated in FP32, so a correct kernel's
+# error is FP32 rounding: a regression bound much tighter than the 2e-3 contract
+BF16_TIGHT = 1e-5
+
+
+def abs_values(va: np.ndarray, dtype: str) -> np.ndarray:
+    """|values| in the stored encoding (BF16: sign bit cleared)."""
+    if dtype == "bf16":
+        return (va.view(np.uint16) & np.uint16(0x7FFF)).astype(np.uint16)
+    return np.abs(va)
+
+
+def check_all_rows(y, rp, co, va, dtype: str, x, what=""):
+    """Every row of y = A x against the FP64 oracle on the stored values:
+    relative L2 within TOL (and BF16_TIGHT for BF16 values), and per row
+    |y_i - y_i*| <= (2 n_i + 2) u sum_j |a_ij x_j| -- the rounding bound of any
+    order of the row's n_i products and at most 2 n_i + 1 additions (entries,
+    partial sums of split rows and halves), u the accumulation's unit roundoff.
+    So one wrong row cannot hide in the norm."""
+    y = np.asarray(y, dtype=np.float64)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    M = len(rp) - 1
+    ref = oracle.spmv(M, rp, co, va, code(dtype), x)
+    mag = oracle.spmv(M, rp, co, abs_values(va, dtype), code(dtype), np.abs(x))
+    n = np.diff(np.asarray(rp, dtype=np.int64))
+    bound = (2 * n + 2) * UNIT[dtype] * mag * 1.01
+    bad = np.abs(y - ref) > bound
+    assert not bad.any(), (what, int(bad.sum()), int(np.argmax(bad)))
+    err = rel_l2(y, ref)
+    assert err <= TOL[dtype], (what, err)
+    if dtype == "bf16":
+        assert err <= BF16_TIGHT, (what, err)
+    return err

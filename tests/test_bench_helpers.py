@@ -1,6 +1,7 @@
-"""The benchmark's bookkeeping, on CPU: algorithmic bytes, the committed ncu
-traffic it quotes (and the kernel revision those counters belong to), the
-host record of CPU numbers."""
+"""The benchmark's bookkeeping, on CPU: algorithmic bytes, the ncu traffic
+records it quotes (tied to the hash of the kernel's sources), the host record
+of CPU numbers."""
+import json
 import os
 import sys
 
@@ -19,12 +20,28 @@ def test_algorithmic_bytes_count_every_byte_once():
     assert bench.alg_bytes(1 << 20, 1 << 20, 25394653, 4, 4, 4) == 215740140
 
 
-@pytest.mark.parametrize("kernel", sorted(bench.KERNEL_REVISION))
-def test_profiles_match_the_kernel_revisions_the_bench_quotes(kernel):
-    traffic, rev = bench.traffic_from_profile(bench.PROFILE_OF[kernel])
-    assert rev == bench.KERNEL_REVISION[kernel], "profile taken on another revision of the kernel"
-    # DRAM bytes per launch near the algorithmic bytes of the profiled product
-    assert 0.95 * 215740140 <= traffic <= 1.1 * 215740140
+def _fake_ncu_csv(path, kernel_name, read_mb, write_mb):
+    hdr = ["ID", "Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum"]
+    units = ["", "", "Mbyte", "Mbyte", "nsecond"]
+    rows = [hdr, units, ["0", kernel_name, f"{read_mb:,.3f}", f"{write_mb:,.3f}", "85,000"],
+            ["1", "other_kernel", "1", "1", "1"]]
+    with open(path, "w") as f:
+        for r in rows:
+            f.write(",".join(f'"{c}"' for c in r) + "\n")
+
+
+@pytest.mark.parametrize("kernel", sorted(bench.KERNEL_SOURCES))
+def test_traffic_records_are_tied_to_the_kernel_sources(kernel, tmp_path):
+    csv = tmp_path / "raw.csv"
+    _fake_ncu_csv(csv, f"void maxe::{kernel}<float, float, 2, false>(Params)", 1227.5, 3.1)
+    rec = bench.record_profile(str(csv), kernel, 0, "ncu ...", "powerlaw", out_dir=str(tmp_path))
+    assert rec["traffic_bytes_per_launch"] == pytest.approx(1230.6e6)
+    assert rec["source_sha256"] == bench.kernel_source_hash(kernel)
+    assert bench.traffic_from_record(kernel, str(tmp_path)) == pytest.approx(1230.6e6)
+    # a record taken on other sources is not quoted
+    rec["source_sha256"] = "0" * 64
+    (tmp_path / bench.PROFILE_RECORD[kernel]).write_text(json.dumps(rec))
+    assert bench.traffic_from_record(kernel, str(tmp_path)) is None
 
 
 def test_host_record():

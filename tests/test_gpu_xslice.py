@@ -1,7 +1,8 @@
 """GPU parity of the x-sliced SpMV (x staged in shared memory by column slices,
-rows owned by warps): products within the FP tolerance of the FP64 oracle in
-both spaces, deterministic, with tiles looping over CTAs, and the CSR kernel
-taking over for unaligned x."""
+rows owned by warps, tiles on one CTA or on a cluster of two CTAs that split
+the columns): every row within the FP tolerance of the FP64 oracle in both
+spaces, deterministic, with more tiles than SMs, and the CSR kernel taking over
+for unaligned x."""
 import numpy as np
 import pytest
 import torch
@@ -9,7 +10,7 @@ import torch
 import oracle
 from paper_2308_00106_gb300 import maxe
 from paper_2308_00106_gb300 import workloads as W
-from tests.gpu_common import EDGE_KINDS, TOL, code, edge_matrix, oracle_permuted, rel_l2
+from tests.gpu_common import EDGE_KINDS, TOL, check_all_rows, code, edge_matrix, oracle_permuted, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -23,43 +24,45 @@ def _perms(A, seed):
     return maxe.maxe_build_permutation(seed, A.rows, 0), maxe.maxe_build_permutation(seed, A.cols, 1)
 
 
+@pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("kind", EDGE_KINDS + ["mixed"])
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
-def test_xslice_spmv_against_oracle(kind, dtype):
+def test_xslice_spmv_against_oracle(kind, dtype, pairs):
     if kind == "mixed":
         L = np.random.default_rng(7).choice([0, 1, 7, 8, 9, 255, 256, 257, 900], 3000)
         A = W.from_lengths(7, L, 40000, dtype)
     else:
         A = edge_matrix(kind, dtype, seed=8)
     rperm, cperm = _perms(A, 31)
-    h = maxe.from_csr(A.to("cuda"), rperm, cperm, xslice=True)
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, xslice=True, xs_pairs=pairs)
     assert h.xslice() == (A.nnz > 0)
+    assert h.xslice_pairs() == (A.nnz > 0 and pairs and dtype != "f64")  # FP64 values never run pairs
     vd = "f64" if dtype == "f64" else "f32"
     x = W.vector(9, A.cols, vd, "cuda")
     rp, co, va = A.numpy()
     y = torch.full((A.rows,), float("nan"), dtype=x.dtype, device="cuda")
     maxe.maxe_spmv(h, x, y)  # original space: x gathered, y scattered through rperm
     assert not torch.isnan(y).any()
-    assert rel_l2(y.cpu().numpy(), oracle.spmv(A.rows, rp, co, va, code(dtype), x.cpu().numpy())) <= TOL[dtype]
+    check_all_rows(y.cpu().numpy(), rp, co, va, dtype, x.cpu().numpy(), "original space")
     nrp, nco, nva = oracle_permuted(A, rperm, cperm)
     xp = x[cperm.long()].contiguous()
     yp = maxe.maxe_spmv(h, xp, permuted=True)
-    assert rel_l2(yp.cpu().numpy(), oracle.spmv(A.rows, nrp, nco, nva, code(dtype), xp.cpu().numpy())) <= TOL[dtype]
+    check_all_rows(yp.cpu().numpy(), nrp, nco, nva, dtype, xp.cpu().numpy(), "permuted space")
+    assert torch.equal(maxe.maxe_spmv(h, xp, permuted=True), yp)  # deterministic
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64", "bf16"])
 def test_xslice_many_tiles_per_cta(dtype):
-    """More row tiles than SMs (the 5-point Laplacian, 2.9M rows): CTAs loop over
-    tiles and the slice ring's phases carry across them."""
+    """More row tiles than SMs (the 5-point Laplacian, 2.9M rows: the tiles are
+    bounded by the accumulators that fit in shared memory), so the CTAs run in
+    several waves; natural order keeps the cells large (the prefetch cursor)."""
     A = W.laplacian5(1700, dtype, "cuda")
     h = maxe.from_csr(A, xslice=True)
-    assert h.xslice() and h.xslice_prefetch()  # natural order: large cells, the prefetch cursor runs
+    assert h.xslice() and h.xslice_prefetch() and not h.xslice_pairs()  # banded: uneven column halves
     x = W.vector(3, A.cols, "f64" if dtype == "f64" else "f32", "cuda")
     y = maxe.maxe_spmv(h, x)
     rp, co, va = A.numpy()
-    rows = np.random.default_rng(1).choice(A.rows, 4000, replace=False)
-    ref = oracle.spmv_rows(rp, co, va, code(dtype), x.cpu().numpy(), rows)
-    assert rel_l2(y.cpu().numpy()[rows], ref) <= TOL[dtype]
+    check_all_rows(y.cpu().numpy(), rp, co, va, dtype, x.cpu().numpy())
     ones = maxe.maxe_spmv(h, torch.ones(A.cols, dtype=x.dtype, device="cuda")).cpu().numpy().reshape(1700, 1700)
     ref1 = np.zeros((1700, 1700))
     ref1[0, :] += 1
@@ -69,20 +72,21 @@ def test_xslice_many_tiles_per_cta(dtype):
     np.testing.assert_array_equal(ones, ref1)
 
 
-def test_xslice_powerlaw_deterministic_and_matches_csr():
+@pytest.mark.parametrize("pairs", [None, False])
+def test_xslice_powerlaw_deterministic_and_matches_csr(pairs):
     A = W.powerlaw(5, n=400000, device="cuda")
     rperm, cperm = _perms(A, 5)
-    h = maxe.from_csr(A, rperm, cperm, xslice=True)
+    h = maxe.from_csr(A, rperm, cperm, xslice=True, xs_pairs=pairs)
     hc = maxe.from_csr(A, rperm, cperm)
     assert h.xslice() and not hc.xslice()
-    assert not h.xslice_prefetch()  # permuted: ~100-entry cells, no prefetch cursor
+    assert h.xslice_pairs() == (pairs is None)  # permuted: the column halves of every tile are even
+    assert not h.xslice_prefetch()  # permuted: small cells, no prefetch cursor
     x = W.vector(4, A.cols, "f32", "cuda")
     y1 = maxe.maxe_spmv(h, x)
     assert torch.equal(maxe.maxe_spmv(h, x), y1)
     assert rel_l2(y1.cpu().numpy(), maxe.maxe_spmv(hc, x).cpu().numpy()) <= 1e-6
     rp, co, va = A.numpy()
-    rows = np.random.default_rng(2).choice(A.rows, 3000, replace=False)
-    assert rel_l2(y1.cpu().numpy()[rows], oracle.spmv_rows(rp, co, va, code("f32"), x.cpu().numpy(), rows)) <= TOL["f32"]
+    check_all_rows(y1.cpu().numpy(), rp, co, va, "f32", x.cpu().numpy())
     # x not 16-byte aligned: the CSR kernel runs instead, same result within FP32 rounding
     xb = torch.empty(A.cols + 1, device="cuda")
     xb[1:] = x[cperm.long()]
@@ -101,26 +105,25 @@ def test_xslice_autotune_keeps_the_faster_kernel():
     h = maxe.from_csr(A, *_perms(A, 6), autotune=True)
     x = W.vector(5, A.cols, "f32", "cuda")
     rp, co, va = A.numpy()
-    rows = np.random.default_rng(3).choice(A.rows, 2000, replace=False)
     y = maxe.maxe_spmv(h, x)
-    assert rel_l2(y.cpu().numpy()[rows], oracle.spmv_rows(rp, co, va, code("f32"), x.cpu().numpy(), rows)) <= TOL["f32"]
+    check_all_rows(y.cpu().numpy(), rp, co, va, "f32", x.cpu().numpy())
 
 
+@pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("permuted", [False, True])
-def test_xslice_pad_entries_keep_infinite_x_out_of_other_rows(dtype, permuted):
-    """The slots after the lane runs of a cell read the zero column after each
-    slice, not x: infinities in x reach only the rows that have entries in
-    those columns.  The infinities sit on the first column of every slice and
-    on the last column."""
+def test_xslice_infinite_x_reaches_only_its_rows(dtype, permuted, pairs):
+    """Lanes without an entry in a step compute nothing: infinities in x reach
+    only the rows that have entries in those columns.  The infinities sit on the
+    first column of every slice (of both slice widths) and on the last column."""
     lengths = np.random.default_rng(12).integers(0, 40, 5000)
     A = W.from_lengths(12, lengths, 40000, dtype)
     rperm, cperm = _perms(A, 13) if permuted else (None, None)
-    h = maxe.from_csr(A.to("cuda"), rperm, cperm, xslice=True)
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, xslice=True, xs_pairs=pairs)
     assert h.xslice()
     nrp, nco, nva = oracle_permuted(A, rperm, cperm)
-    sb = 13 if dtype == "f64" else 14
-    bad = np.unique(np.r_[np.arange(0, A.cols, 1 << sb), A.cols - 1])
+    widths = [8192] if dtype == "f64" else [16384, 12288]
+    bad = np.unique(np.r_[np.concatenate([np.arange(0, A.cols, w) for w in widths]), A.cols - 1])
     vd = "f64" if dtype == "f64" else "f32"
     xp = W.vector(14, A.cols, vd, "cuda")
     xp[torch.as_tensor(bad, device="cuda")] = float("inf")
