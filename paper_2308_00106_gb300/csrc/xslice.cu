@@ -667,15 +667,18 @@ __device__ __forceinline__ int32_t xs_lane_len(int32_t l, int32_t S, int32_t fp)
 
 // One thread per cell: the slot of every sorted entry (outpos).  A cell of at
 // most 32 steps gets its accumulator groups (runs of equal keys) packed whole
-// into the lane runs: the groups of two or more entries, largest first, each
-// into the run with the most room left; then the single entries, in sort
-// order, fill the runs in turn.  If a group does not fit, the cell is tried
-// again dealt over one or two more steps (more room per run).  Otherwise, and
-// in longer cells, the runs cut the sort order where they end; a short cell
-// that cannot be packed is first dealt over S >= m + G steps (m its largest
-// accumulator count), so that a cut accumulator's two lanes meet at least a
-// group boundary apart, as in the long cells.
-constexpr int kXsPackBig = 256;  // groups of two or more entries a cell may have to be packed
+// into the lane runs.  A lane's home is the accumulators of its shared-memory
+// bank (the sort order groups them), so that the lanes of a step update
+// different banks: the groups of two or more entries, largest first, go home
+// when there is room, else into the run with the most room; then the single
+// entries go home, and those whose home is full fill the room left.  If a
+// group does not fit, the cell is tried again dealt over one or two more steps
+// (more room per run).  Otherwise, and in longer cells, the runs cut the sort
+// order where they end; a short cell that cannot be packed is first dealt over
+// S >= m + G steps (m its largest accumulator count), so that a cut
+// accumulator's two lanes meet at least a group boundary apart, as in the long
+// cells.
+constexpr int kXsPackBig = 128;  // groups of two or more entries a cell may have to be packed
 
 __global__ void xs_pack_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ ustart,
                                const int32_t* __restrict__ counts, const int32_t* __restrict__ mult,
@@ -690,11 +693,11 @@ __global__ void xs_pack_kernel(const uint64_t* __restrict__ keys, const int32_t*
   auto slot = [&](int32_t lane, int32_t step, int32_t F, int32_t P) {  // (F, P) of the layout
     return static_cast<int32_t>(st + step * F + (step < P ? step : P) + lane);
   };
+  auto bank = [&](int64_t i) { return static_cast<int>((keys[i] >> 10) & 31u); };
   bool packed = false;
-  if (S <= 32) {
+  if (S <= 32) {  // n <= 1024
     // the groups of two or more entries, largest first (insertion sort, stable)
-    int64_t big_i[kXsPackBig];
-    int32_t big_n[kXsPackBig];
+    int32_t big_i[kXsPackBig], big_n[kXsPackBig];
     int nb = 0;
     bool fits_list = true;
     for (int64_t i = u0; i < u0 + n;) {
@@ -712,7 +715,7 @@ __global__ void xs_pack_kernel(const uint64_t* __restrict__ keys, const int32_t*
           big_n[q] = big_n[q - 1];
           --q;
         }
-        big_i[q] = i;
+        big_i[q] = static_cast<int32_t>(i - u0);
         big_n[q] = m;
       }
       i = j;
@@ -731,31 +734,49 @@ __global__ void xs_pack_kernel(const uint64_t* __restrict__ keys, const int32_t*
         fill[l] = 0;
         room[l] = xs_lane_len(l, S2, fp2);
       }
+      auto place = [&](int64_t i0, int32_t m, int l) {
+        for (int32_t t = 0; t < m; ++t) outpos[i0 + t] = slot(l, fill[l] + t, F, P);
+        fill[l] += m;
+        room[l] -= m;
+      };
       bool ok = true;
-      for (int b = 0; b < nb && ok; ++b) {
-        int best = 0;
-        for (int l = 1; l < 32; ++l)
-          if (room[l] > room[best]) best = l;
-        if (room[best] < big_n[b]) {
+      for (int b = 0; b < nb; ++b) {
+        const int64_t i0 = u0 + big_i[b];
+        int l = bank(i0);
+        if (room[l] < big_n[b]) {
+          l = 0;
+          for (int q = 1; q < 32; ++q)
+            if (room[q] > room[l]) l = q;
+        }
+        if (room[l] < big_n[b]) {
           ok = false;
           break;
         }
-        for (int32_t t = 0; t < big_n[b]; ++t) outpos[big_i[b] + t] = slot(best, fill[best] + t, F, P);
-        fill[best] += big_n[b];
-        room[best] -= big_n[b];
+        place(i0, big_n[b], l);
       }
       if (!ok) continue;
-      int l = 0;
+      uint32_t deferred[32];  // single entries whose home was full (bit per entry of the cell)
+      for (int w = 0; w < 32; ++w) deferred[w] = 0u;
       for (int64_t i = u0; i < u0 + n;) {
         int64_t j = i + 1;
         while (j < u0 + n && keys[j] == keys[i]) ++j;
         if (j - i == 1) {
-          while (l < 31 && room[l] == 0) ++l;  // the rooms add up to the single entries left
-          outpos[i] = slot(l, fill[l], F, P);
-          ++fill[l];
-          --room[l];
+          const int l = bank(i);
+          if (room[l] > 0) {
+            place(i, 1, l);
+          } else {
+            const int32_t r = static_cast<int32_t>(i - u0);
+            deferred[r >> 5] |= 1u << (r & 31);
+          }
         }
         i = j;
+      }
+      int l = 0;
+      for (int w = 0; w < 32; ++w) {
+        for (uint32_t bits = deferred[w]; bits; bits &= bits - 1) {
+          while (l < 31 && room[l] == 0) ++l;  // the rooms add up to the deferred entries
+          place(u0 + 32 * w + __ffs(bits) - 1, 1, l);
+        }
       }
       packed = true;
       if (extra > 0) {
@@ -776,6 +797,70 @@ __global__ void xs_pack_kernel(const uint64_t* __restrict__ keys, const int32_t*
     for (int32_t k = 0; k < n; ++k) {
       const XsRun r = xs_run_of(k, S, fp);
       outpos[u0 + k] = slot(r.lane, r.step, F, P);
+    }
+  }
+}
+
+// One warp per packed cell of full steps (at most 32): the order of each run's
+// entries is free (an accumulator's entries are in one run), so it is chosen
+// step by step to spread the shared-memory banks a step touches: at step s the
+// lanes in turn take, among their remaining entries, the one whose x bank plus
+// accumulator bank is least used at step s so far.  Cells whose runs cut an
+// accumulator keep their order.
+constexpr int kXsOrderWarps = 8;  // warps (cells) per block
+
+__global__ void __launch_bounds__(32 * kXsOrderWarps) xs_order_kernel(
+    const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ ustart, const int32_t* __restrict__ counts, const int32_t* __restrict__ seg,
+    int64_t cells, int32_t* __restrict__ outpos) {
+  __shared__ int32_t use_x[kXsOrderWarps][32], use_a[kXsOrderWarps][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = static_cast<int64_t>(blockIdx.x) * kXsOrderWarps + w;
+  if (c >= cells) return;  // the whole warp leaves together
+  const int32_t n = counts[c], S = seg[cells + c], fp = seg[2 * cells + c];
+  if (n == 0 || S > 32 || fp >= 0) return;  // full-step cells only
+  const int32_t st = seg[c];
+  const int64_t u0 = ustart[c];
+  bool cut = false;  // packed cells only: no accumulator cut between two runs
+  for (int64_t i = u0 + lane; i < u0 + n; i += 32) {
+    const bool next_same = i + 1 < u0 + n && keys[i + 1] == keys[i];
+    if (next_same && ((outpos[i] - st) & 31) != ((outpos[i + 1] - st) & 31)) cut = true;
+  }
+  if (__any_sync(0xffffffffu, cut)) return;
+  // this lane's run: its entries' sorted positions and banks
+  int32_t mine_i[32];
+  uint8_t mine_x[32], mine_a[32];
+  int m = 0;
+  for (int64_t i = u0; i < u0 + n; ++i) {
+    if (((outpos[i] - st) & 31) != lane) continue;
+    mine_i[m] = static_cast<int32_t>(i - u0);
+    mine_x[m] = static_cast<uint8_t>(col[vals[i]] & 31);
+    mine_a[m] = static_cast<uint8_t>((keys[i] >> 10) & 31u);
+    ++m;
+  }
+  uint32_t taken = 0;
+  __syncwarp();
+  for (int s = 0; s < S; ++s) {
+    use_x[w][lane] = 0;
+    use_a[w][lane] = 0;
+    __syncwarp();
+    for (int turn = 0; turn < 32; ++turn) {
+      if (lane == turn && s < m) {
+        int best = -1, best_cost = 1 << 30;
+        for (int t = 0; t < m; ++t) {
+          if ((taken >> t) & 1u) continue;
+          const int cost = use_x[w][mine_x[t]] + use_a[w][mine_a[t]];
+          if (cost < best_cost) {
+            best_cost = cost;
+            best = t;
+          }
+        }
+        taken |= 1u << best;
+        ++use_x[w][mine_x[best]];
+        ++use_a[w][mine_a[best]];
+        outpos[u0 + mine_i[best]] = st + 32 * s + lane;
+      }
+      __syncwarp();
     }
   }
 }
@@ -1183,6 +1268,9 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool force_pair, 
   MAXE_CUDA_TRY(cudaMemsetAsync(xval, 0, static_cast<size_t>(vb) * (Zp + kXsSlack), st));
   xs_pack_kernel<<<static_cast<unsigned>(ceil_div(cells, 128)), 128, 0, st>>>(keys, d_ustart, counts, mult, d_seg,
                                                                               cells, G, outpos);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  xs_order_kernel<<<static_cast<unsigned>(ceil_div(cells, kXsOrderWarps)), 32 * kXsOrderWarps, 0, st>>>(
+      keys, vals, h->col, d_ustart, counts, d_seg, cells, outpos);
   MAXE_CUDA_TRY(cudaGetLastError());
   xs_scatter_kernel<<<static_cast<unsigned>(ceil_div(Z, 256)), 256, 0, st>>>(keys, vals, Z, outpos, h->col, h->val,
                                                                              vb, SC, nS, idx, xval);
