@@ -97,7 +97,7 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * runs on a cluster of two CTAs, one per half, whose sums are added in a fixed
  * order.  Costs 4 + value-size bytes per entry more memory (plus 12 bytes of
  * descriptor per (row range, slice) cell) and a synchronising build.
- * MAXE_AUTOTUNE builds it too when its x traffic would stay under four times
+ * MAXE_AUTOTUNE builds it too when its x traffic would stay under eight times
  * the matrix, and keeps it only if it times faster than the CSR kernel.
  * Ignored with MAXE_EQUAL_ROWS.  Deterministic. */
 #define MAXE_XSLICE 0x80u
@@ -107,6 +107,13 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * never use pairs); MAXE_XS_SINGLE never does.  Not both. */
 #define MAXE_XS_PAIRS 0x100u
 #define MAXE_XS_SINGLE 0x200u
+/* Flag of maxe_permute_csr: SpMM (k > 1) with one row per group of lanes --
+ * each lane holds 16 bytes of the k columns of X and Y (4 FP32 / 2 FP64), a
+ * group walks its row's entries and writes its piece of Y once -- for matrices
+ * with short rows, when X and Y are 16-byte aligned and ldx, ldy are multiples
+ * of 4 (FP32 vectors) / 2 (FP64) (tuning override; MAXE_AUTOTUNE times it
+ * against the other SpMM paths at k = 16 and keeps the fastest). */
+#define MAXE_SPMM_ROWS 0x400u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -191,7 +198,8 @@ MAXE_API maxe_status maxe_permute_scatter(const int32_t* perm, int32_t n, int32_
  * bit for bit.  rperm (rows) / cperm (cols): (device) int32, NULL = identity
  * (the "plain" matrix).  The handle keeps its own copies of the permutations.
  * flags: any of MAXE_VALIDATE, MAXE_AUTOTUNE, MAXE_ITEMS16, MAXE_SPMM_LANES,
- * MAXE_EQUAL_ROWS, MAXE_COO, MAXE_XSLICE, MAXE_XS_PAIRS, MAXE_XS_SINGLE.  *out receives the new handle.
+ * MAXE_EQUAL_ROWS, MAXE_COO, MAXE_XSLICE, MAXE_XS_PAIRS, MAXE_XS_SINGLE,
+ * MAXE_SPMM_ROWS.  *out receives the new handle.
  * Synchronises `stream` once (to size the pass over rows longer than 2048).
  * Errors: INVALID on bad sizes/NULL pointers (or failed validation), OOM. */
 MAXE_API maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int32_t* cperm,
@@ -209,7 +217,8 @@ MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, c
  * (8 or 16), plus 0x100 when SpMM uses columns across lanes, plus 0x200 when
  * SpMV uses the x-sliced form (MAXE_XSLICE), plus 0x400 when that form's cells
  * are large enough for its L2 prefetch cursor, plus 0x800 when it runs its tiles
- * on pairs of CTAs (column halves).  items: (host). */
+ * on pairs of CTAs (column halves), plus 0x1000 when SpMM takes one row per
+ * group of lanes (MAXE_SPMM_ROWS).  items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;
@@ -327,14 +336,24 @@ MAXE_API maxe_status maxe_batch_set(maxe_batch* b, const maxe_batch_item* items,
 /* Upload the table and launch the persistent kernel(s) on `stream`. */
 MAXE_API maxe_status maxe_batch_run(maxe_batch* b, void* stream);
 MAXE_API maxe_status maxe_batch_destroy(maxe_batch* b);
-/* Autotune the handle's batch plan for k right-hand sides: for entries per
- * task in {512, 2048, 8192, 32768} (and 8 or 16 entries per lane when k = 1)
- * time batches of copies of the item that fill the GPU several times over,
- * and keep the plan with the best throughput.  Synchronises `stream`. */
+/* Autotune the handle's batch plan for k right-hand sides.  Two batches of
+ * copies of the item, whose tasks under the current plan fill the resident
+ * warps once and four times over, are timed (the best of three timings each;
+ * every plan on the same copies) for: the handle's current plan; entries per task
+ * (rows per warp task) in {512, 2048, 8192, 32768} (at least nnz / resident
+ * warps) x the kernel variant (8 or 16 entries per lane for k = 1, column
+ * passes or columns across lanes for k > 1); then, for the best of those, the
+ * CTA shape of the launch (fewer CTAs per SM than fit).  The current plan is
+ * replaced only by one at least 3% faster at both fills, so tuning never keeps
+ * a slower plan.  In a batch, a launch uses the largest CTA count per SM its items'
+ * plans ask for (all that fit if any item has the default).  Results do not
+ * depend on the plan's CTA shape.  Synchronises `stream`. */
 MAXE_API maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream);
 /* The handle's batch plan (any output may be NULL). */
 MAXE_API maxe_status maxe_batch_plan_info(const maxe_handle* h, int64_t* entries_per_task, int32_t* tasks,
                                           int32_t* items_per_lane);
+/* CTAs per SM the handle's batch plan asks of a launch (0: as many as fit). */
+MAXE_API maxe_status maxe_batch_plan_shape(const maxe_handle* h, int32_t* blocks_per_sm);
 
 /* Power iteration on a square handle, in the original space (v <- A v / ||A v||_2,
  * `steps` times from v0, then lambda = v^T A v).  Not in the paper: it is the

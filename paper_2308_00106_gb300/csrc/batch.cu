@@ -151,10 +151,13 @@ maxe_status batch_prepare(int* blocks_per_sm) {
   return MAXE_OK;
 }
 
+// bps: CTAs per SM (0: as many as fit).  The grid only changes which warp
+// takes which task, never a task's sums: results do not depend on it.
 template <typename VT, int CLASS>
-maxe_status batch_launch(const BatchParams& bp, int sms, cudaStream_t st) {
+maxe_status batch_launch(const BatchParams& bp, int sms, int bps, cudaStream_t st) {
   int occ = 1;
   MAXE_TRY((batch_prepare<VT, CLASS>(&occ)));
+  if (bps > 0 && bps < occ) occ = bps;
   const int64_t want = ceil_div(bp.ntasks, kWarps);
   const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * occ)));
   spmm_batch_kernel<VT, CLASS><<<grid, kThreads, BatchClass<VT, CLASS>::warp_smem() * kWarps, st>>>(bp);
@@ -163,19 +166,37 @@ maxe_status batch_launch(const BatchParams& bp, int sms, cudaStream_t st) {
 }
 
 template <typename VT>
-maxe_status batch_launch_class(int cls, const BatchParams& bp, int sms, cudaStream_t st) {
-  if (cls == 0) return batch_launch<VT, 0>(bp, sms, st);
-  if (cls == 1) return batch_launch<VT, 1>(bp, sms, st);
-  return batch_launch<VT, 2>(bp, sms, st);
+maxe_status batch_launch_class(int cls, const BatchParams& bp, int sms, int bps, cudaStream_t st) {
+  if (cls == 0) return batch_launch<VT, 0>(bp, sms, bps, st);
+  if (cls == 1) return batch_launch<VT, 1>(bp, sms, bps, st);
+  return batch_launch<VT, 2>(bp, sms, bps, st);
 }
 
-maxe_status launch_for(maxe_dtype d, int cls, const BatchParams& bp, int sms, cudaStream_t st) {
+maxe_status launch_for(maxe_dtype d, int cls, const BatchParams& bp, int sms, int bps, cudaStream_t st) {
   switch (d) {
-    case MAXE_F64: return batch_launch_class<double>(cls, bp, sms, st);
-    case MAXE_F32: return batch_launch_class<float>(cls, bp, sms, st);
-    case MAXE_BF16: return batch_launch_class<uint16_t>(cls, bp, sms, st);
+    case MAXE_F64: return batch_launch_class<double>(cls, bp, sms, bps, st);
+    case MAXE_F32: return batch_launch_class<float>(cls, bp, sms, bps, st);
+    case MAXE_BF16: return batch_launch_class<uint16_t>(cls, bp, sms, bps, st);
   }
   return MAXE_ERR_INVALID;
+}
+
+// CTAs per SM that the batched kernel of (value type, class) fits
+int batch_occupancy(maxe_dtype d, int cls) {
+  int occ = 1;
+  maxe_status s = MAXE_OK;
+  auto one = [&](auto vt) {
+    using VT = decltype(vt);
+    if (cls == 0) s = batch_prepare<VT, 0>(&occ);
+    else if (cls == 1) s = batch_prepare<VT, 1>(&occ);
+    else s = batch_prepare<VT, 2>(&occ);
+  };
+  switch (d) {
+    case MAXE_F64: one(double{}); break;
+    case MAXE_F32: one(float{}); break;
+    case MAXE_BF16: one(uint16_t{}); break;
+  }
+  return s == MAXE_OK ? occ : 1;
 }
 
 // resident warps of the batched kernel (class 0) for one value type
@@ -206,7 +227,7 @@ int pick_vw(const maxe_batch_item& a, int eb) {
 }  // namespace
 
 // Batch plan of a handle: a partition with H_b entries per warp task.
-maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc) {
+maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc, int bps) {
   H = std::max<int64_t>(256, H);
   const int64_t nW = std::max<int64_t>(1, ceil_div(h->nnz, H));
   int32_t* w = static_cast<int32_t*>(h->al.get(static_cast<size_t>(nW + 1) * sizeof(int32_t)));
@@ -223,6 +244,7 @@ maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int
   h->bH = H;
   h->bit16 = it16;
   h->blc = lc;
+  h->bbps = bps;
   return MAXE_OK;
 }
 
@@ -342,6 +364,8 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
     int32_t* ht = b->h_task0 + static_cast<size_t>(g) * (b->capacity + 1);
     int32_t m = 0;
     int64_t tasks = 0;
+    int bps = 0;  // the largest CTA count per SM the items' plans ask for (0: as many as fit)
+    bool any_default = false;
     for (const maxe_batch_item& a : b->items) {
       const maxe_handle* h = a.h;
       if (h->dtype != types[ti] || h->rows == 0) continue;
@@ -371,7 +395,12 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
       ht[m] = static_cast<int32_t>(tasks);
       tasks += h->bnW;
       ++m;
+      if (h->bbps == 0)
+        any_default = true;
+      else
+        bps = std::max(bps, h->bbps);
     }
+    if (any_default) bps = 0;
     if (m == 0) continue;
     if (tasks > INT32_MAX) return MAXE_ERR_UNSUPPORTED;
     ht[m] = static_cast<int32_t>(tasks);
@@ -381,7 +410,7 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
     MAXE_CUDA_TRY(cudaMemcpyAsync(dt, ht, sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, st));
     MAXE_CUDA_TRY(cudaMemsetAsync(b->d_next + g, 0, sizeof(int32_t), st));
     BatchParams bp{di, dt, b->status, b->d_next + g, m, static_cast<int32_t>(tasks), wait_limit_ns()};
-    MAXE_TRY(launch_for(types[ti], cls, bp, b->sms, st));
+    MAXE_TRY(launch_for(types[ti], cls, bp, b->sms, bps, st));
   }
   if (cap == cudaStreamCaptureStatusNone) {
     MAXE_CUDA_TRY(cudaEventRecord(b->uploaded, st));
@@ -415,49 +444,98 @@ maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
                                                                                              : MAXE_ERR_CUDA;
   const int64_t resident = batch_resident_warps(h->dtype, h->sms);
   const int64_t floor_h = ceil_div(h->nnz, resident);
+  struct Plan {
+    int64_t H;
+    int it16, lc, bps;
+  };
+  // the plan the handle has (the default unless tuned before)
+  const Plan current{h->bH, h->bit16, h->blc, h->bbps};
+  maxe_batch_item items[kMaxCopies];
+  // Throughput, not latency: the matrix is timed as one of many items, so the
+  // item is repeated until the current plan's tasks fill the resident warps
+  // once and four times over; every plan is timed on the same copies, that is
+  // on the same work (the copies write identical values to one Y; only the
+  // time is used).  Returns ms per copy, the best of three timings of 3 runs.
+  const int64_t copies1 = std::max<int64_t>(1, std::min<int64_t>(kMaxCopies, ceil_div(resident, h->bnW)));
+  const int64_t copies4 = std::max<int64_t>(1, std::min<int64_t>(kMaxCopies, ceil_div(4 * resident, h->bnW)));
+  auto time_fill = [&](int fill, float* per_copy) -> maxe_status {
+    const int64_t copies = fill == 1 ? copies1 : copies4;
+    for (int64_t c = 0; c < copies; ++c) items[c] = maxe_batch_item{h, k, X, kp, Y, kp, 0u};
+    MAXE_TRY(maxe_batch_set(b, items, static_cast<int32_t>(copies)));
+    for (int rep = 0; rep < 2; ++rep) MAXE_TRY(maxe_batch_run(b, stream));
+    float best = 1e30f;
+    for (int trial = 0; trial < 3; ++trial) {
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3; ++rep) MAXE_TRY(maxe_batch_run(b, stream));
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return MAXE_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms / static_cast<float>(copies));
+    }
+    *per_copy = best;
+    return MAXE_OK;
+  };
+  // A plan is timed in a batch that fills the GPU about once (where large
+  // tasks leave a tail) and four times over (where they do not).
+  auto time_plan = [&](const Plan& pl, float* t1, float* t4) -> maxe_status {
+    MAXE_TRY(batch_plan(h, pl.H, pl.it16, st, pl.lc, pl.bps));
+    MAXE_TRY(time_fill(1, t1));
+    return time_fill(4, t4);
+  };
+  float c1 = 1e30f, c4 = 1e30f;
+  if (s == MAXE_OK) s = time_plan(current, &c1, &c4);
+  // a candidate's score: its slower side relative to the current plan
+  auto score = [&](float t1, float t4) { return std::max(t1 / c1, t4 / c4); };
+  Plan best = current;
+  float t_best = 1.0f;  // the current plan's score
+  const float t_current = 1.0f;
+  // 1) entries per task and the kernel variant, at the launch's full CTA count
   const int64_t cand_h[4] = {std::max<int64_t>(512, floor_h), std::max<int64_t>(2048, floor_h),
                              std::max<int64_t>(8192, floor_h), std::max<int64_t>(32768, floor_h)};
-  float best = 1e30f;
-  int64_t best_h = cand_h[1];
-  int best_it = 0, best_lc = 0;
-  // Throughput, not latency: the matrix is timed as one of many items, so the
-  // item is repeated until its tasks fill the GPU a few times over (the copies
-  // write identical values to one Y; only the time is used).
-  maxe_batch_item items[kMaxCopies];
   for (int ci = 0; ci < 4 && s == MAXE_OK; ++ci) {
     if (ci > 0 && cand_h[ci] == cand_h[ci - 1]) continue;
     for (int var = 0; var <= 1 && s == MAXE_OK; ++var) {
       // second variant: 16 entries per lane for k = 1, columns across lanes for k > 1
-      const int it16 = (k == 1) ? var : 0, lc = (k > 1) ? var : 0;
+      const Plan pl{cand_h[ci], (k == 1) ? var : 0, (k > 1) ? var : 0, 0};
       if (var == 1 && k > 1 && lc_group(k, eb, kp % 1024, kp % 1024) == 0) continue;
-      s = batch_plan(h, cand_h[ci], it16, st, lc);
-      if (s != MAXE_OK) break;
-      const int64_t copies = std::max<int64_t>(1, std::min<int64_t>(kMaxCopies, ceil_div(4 * resident, h->bnW)));
-      for (int64_t c = 0; c < copies; ++c) items[c] = maxe_batch_item{h, k, X, kp, Y, kp, 0u};
-      s = maxe_batch_set(b, items, static_cast<int32_t>(copies));
-      for (int rep = 0; rep < 2 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
-      if (s != MAXE_OK) break;
-      cudaEventRecord(e0, st);
-      for (int rep = 0; rep < 3 && s == MAXE_OK; ++rep) s = maxe_batch_run(b, stream);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) s = MAXE_ERR_CUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      const float per_copy = ms / static_cast<float>(copies);
-      if (s == MAXE_OK && per_copy < best) {
-        best = per_copy;
-        best_h = cand_h[ci];
-        best_it = it16;
-        best_lc = lc;
+      if (pl.H == current.H && pl.it16 == current.it16 && pl.lc == current.lc && pl.bps == current.bps) continue;
+      float t1 = 0.f, t4 = 0.f;
+      s = time_plan(pl, &t1, &t4);
+      if (s == MAXE_OK && score(t1, t4) < t_best) {
+        t_best = score(t1, t4);
+        best = pl;
       }
+    }
+  }
+  // 2) CTAs per SM (the CTA shape of the launch) for the best of those
+  const int cls = (k == 1) ? (best.it16 ? 1 : 0) : 2;
+  const int occ = batch_occupancy(h->dtype, cls);
+  const Plan base = best;
+  for (int bps = occ - 1; bps >= 1 && s == MAXE_OK; --bps) {
+    Plan pl = base;
+    pl.bps = bps;
+    float t1 = 0.f, t4 = 0.f;
+    s = time_plan(pl, &t1, &t4);
+    if (s == MAXE_OK && score(t1, t4) < t_best) {
+      t_best = score(t1, t4);
+      best = pl;
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   maxe_batch_destroy(b);
-  if (s == MAXE_OK) s = batch_plan(h, best_h, best_it, st, best_lc);
+  // the handle's plan stays unless a candidate was at least 3% faster at both fills
+  if (t_best > 0.97f * t_current) best = current;
+  if (s == MAXE_OK) s = batch_plan(h, best.H, best.it16, st, best.lc, best.bps);
   if (s == MAXE_OK && cudaStreamSynchronize(st) != cudaSuccess) s = MAXE_ERR_CUDA;
   return s;
+}
+
+maxe_status maxe_batch_plan_shape(const maxe_handle* h, int32_t* blocks_per_sm) {
+  if (!h || !blocks_per_sm) return MAXE_ERR_INVALID;
+  *blocks_per_sm = h->bbps;
+  return MAXE_OK;
 }
 
 maxe_status maxe_batch_plan_info(const maxe_handle* h, int64_t* entries_per_task, int32_t* tasks,

@@ -29,12 +29,14 @@ struct maxe_handle {
   int32_t nW[2] = {0, 0};
   int spmv_items16 = 0;                    // chosen SpMV variant (autotuned or 0)
   int spmm_lc = 0;                         // SpMM with columns across lanes (autotuned or 0)
+  int spmm_rows = 0;                       // SpMM with one row per lane group (autotuned or 0)
   int equal_rows = 0;                      // SpMV partition: equal rows per warp (not equal nonzeros)
   int32_t* bwrow = nullptr;                // batch plan: partition with bH entries per warp task
   int32_t bnW = 0;
   int64_t bH = 0;
   int bit16 = 0;                           // batch plan: 16 entries per lane for k = 1
   int blc = 0;                             // batch plan: SpMM with columns across lanes
+  int bbps = 0;                            // batch plan: CTAs per SM of its launch (0: as many as fit)
   // x-sliced SpMV form (MAXE_XSLICE): entries grouped by ((tile, half, warp range), column slice)
   uint32_t* xs_idx = nullptr;              // (accumulator << 15) | column in slice, step-major cells
   void* xs_val = nullptr;
@@ -82,8 +84,14 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st);
 
 // batch.cu
 constexpr int64_t kDefaultBatchTask = 2048;  // entries per warp task of the default batch plan
-maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc);
+maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int lc, int bps = 0);
 maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st);
+
+// spmm_rows.cu: Y = A' X with one row per group of lanes (short rows), when X
+// and Y are 16-byte aligned with whole 16-byte pieces per row.
+bool spmm_rows_ready(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, const void* Y, int64_t ldy);
+maxe_status spmm_rows_launch(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                             const int32_t* yperm, cudaStream_t st);
 
 // xslice.cu: build the x-sliced form (unless forced, leaves it unbuilt when it
 // would not pay; pairs: > 0 column halves on CTA pairs, 0 when the halves are

@@ -177,6 +177,8 @@ maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t 
   }
   const bool unit = k == 1 && ldx == 1 && ldy == 1;
   if (unit && variant < 0 && lc < 0 && xslice_ready(h, X)) return xslice_launch(h, X, Y, yperm, st);
+  if (k > 1 && variant < 0 && lc < 0 && h->spmm_rows && spmm_rows_ready(h, k, X, ldx, Y, ldy))
+    return spmm_rows_launch(h, k, X, ldx, Y, ldy, yperm, st);
   const int it = (unit && variant < 0) ? h->spmv_items16 : (variant > 0 ? 1 : 0);
   if (it == 1 && !unit) return MAXE_ERR_UNSUPPORTED;
   p.wrow = h->wrow[it];
@@ -248,10 +250,14 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st) {
     void* Y = h->al.get(static_cast<size_t>(h->rows) * k * eb);
     if (X && Y) {
       s = cudaMemsetAsync(X, 0, static_cast<size_t>(h->cols) * k * eb, st) == cudaSuccess ? MAXE_OK : MAXE_ERR_CUDA;
-      float t_pass = 0.f, t_lc = 0.f;
+      float t_pass = 0.f, t_lc = 0.f, t_rows = 0.f;
       if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 0); }, &t_pass);
       if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 1); }, &t_lc);
-      if (s == MAXE_OK) h->spmm_lc = t_lc < t_pass ? 1 : 0;
+      if (s == MAXE_OK) s = timed([&] { return spmm_rows_launch(h, k, X, k, Y, k, nullptr, st); }, &t_rows);
+      if (s == MAXE_OK) {
+        h->spmm_lc = t_lc < t_pass ? 1 : 0;
+        h->spmm_rows = t_rows < std::min(t_pass, t_lc) ? 1 : 0;
+      }
     }
     h->al.put(Y);
     h->al.put(X);

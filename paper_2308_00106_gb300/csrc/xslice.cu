@@ -47,7 +47,7 @@
 // the result is deterministic.  The format is built once from the handle's CSR;
 // it pays when the rows of a tile hit most x sectors of the slices they touch,
 // i.e. for matrices with many nonzeros per column of a tile, and unless asked
-// for explicitly it is skipped when the estimated x traffic exceeds four times
+// for explicitly it is skipped when the estimated x traffic exceeds eight times
 // the matrix.
 #include <algorithm>
 #include <mutex>
@@ -60,8 +60,9 @@ namespace {
 
 constexpr int kXsWarps = 15;  // consumer warps per CTA; with the producer, 4 warps per SM sub-partition
 constexpr int kXsThreads = 32 * (kXsWarps + 1);
-constexpr int kXsColBits = 15;  // idx = (accumulator << 15) | column in slice
-constexpr uint32_t kXsColMask = (1u << kXsColBits) - 1u;
+constexpr int kXsColBits = 15;  // idx = (accumulator << 15) | continues << 14 | column in slice
+constexpr uint32_t kXsColMask = (1u << 14) - 1u;  // slices are at most 16384 columns
+constexpr uint32_t kXsCont = 1u << 14;  // same accumulator as the lane's previous step in the group
 constexpr int kXsSlack = 256;     // zeroed entries after the last cell (L2 prefetches round out to 16 bytes)
 constexpr int kXsMaxSlots = 32767;  // accumulators per CTA (the sort key holds 15 bits of accumulator)
 constexpr int kXsVirtDiv = 96;    // rows with more than 1/96 of their warp's entries are split
@@ -88,7 +89,7 @@ template <>
 struct XsCfg<double, 1> {
   static constexpr int kSliceCols = 8192;  // 64 KB
   static constexpr int kBuffers = 2;
-  static constexpr int kSteps = 8;
+  static constexpr int kSteps = 6;
 };
 
 template <typename VT, int J>
@@ -357,19 +358,40 @@ __device__ __forceinline__ void xs_prefetch(const XsParams& p, const XsPos& q, i
 }
 
 // acc[a] += value * x[column] for the lane's steps of the group, then the
-// warp synchronises (the only place where two lanes' updates of one
-// accumulator meet: the builder keeps them in different groups).
+// warp synchronises (where two lanes' updates of one accumulator meet: the
+// builder keeps them in different groups).  FP64: steps that continue the
+// previous step's accumulator (kXsCont) add into a register, the accumulator
+// is read at the first step of a run and written after its last (each FP64
+// accumulator access costs two shared-memory wavefronts, so this pays there;
+// in FP32 the per-lane branch costs more than the accesses it saves).
 template <typename VT, typename AT, int G>
 __device__ __forceinline__ void xs_compute(const XsGroup<AT, G>& k, const VT* __restrict__ xs, VT* acc) {
   VT xv[G];
 #pragma unroll
   for (int j = 0; j < G; ++j)
     if (j < k.ns) xv[j] = xs[k.id[j] & kXsColMask];
+  if constexpr (sizeof(VT) == 8) {
+    VT sum = VT(0);
+    VT* pa = acc;
 #pragma unroll
-  for (int j = 0; j < G; ++j) {
-    if (j < k.ns) {
-      VT* ap = acc + (k.id[j] >> kXsColBits);
-      *ap = fma(static_cast<VT>(k.a[j]), xv[j], *ap);
+    for (int j = 0; j < G; ++j) {
+      if (j < k.ns) {
+        if (j == 0 || !(k.id[j] & kXsCont)) {  // a new accumulator (the first step of a group always is)
+          if (j > 0) *pa = sum;
+          pa = acc + (k.id[j] >> kXsColBits);
+          sum = *pa;
+        }
+        sum = fma(static_cast<VT>(k.a[j]), xv[j], sum);
+      }
+    }
+    if (k.ns > 0) *pa = sum;
+  } else {
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      if (j < k.ns) {
+        VT* ap = acc + (k.id[j] >> kXsColBits);
+        *ap = fma(static_cast<VT>(k.a[j]), xv[j], *ap);
+      }
     }
   }
   __syncwarp();
@@ -804,15 +826,20 @@ __global__ void xs_pack_kernel(const uint64_t* __restrict__ keys, const int32_t*
 // One warp per packed cell of full steps (at most 32): the order of each run's
 // entries is free (an accumulator's entries are in one run), so it is chosen
 // step by step to spread the shared-memory banks a step touches: at step s the
-// lanes in turn take, among their remaining entries, the one whose x bank plus
-// accumulator bank is least used at step s so far.  Cells whose runs cut an
-// accumulator keep their order.
+// lanes in turn take, among their remaining entries, the cheapest.  Without
+// register runs (FP32 kernels) the cost is how often the entry's x bank plus
+// its accumulator's bank are used at step s so far.  With register runs
+// (FP64: cont = true) an entry that continues the lane's previous accumulator
+// inside a register group touches no accumulator (cost: its x bank's uses);
+// any other costs that plus two accesses of its accumulator's bank (one more
+// for each earlier use).  Cells whose runs cut an accumulator keep their
+// order.
 constexpr int kXsOrderWarps = 8;  // warps (cells) per block
 
 __global__ void __launch_bounds__(32 * kXsOrderWarps) xs_order_kernel(
     const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals, const int32_t* __restrict__ col,
     const int32_t* __restrict__ ustart, const int32_t* __restrict__ counts, const int32_t* __restrict__ seg,
-    int64_t cells, int32_t* __restrict__ outpos) {
+    int64_t cells, int G, bool cont_runs, int32_t* __restrict__ outpos) {
   __shared__ int32_t use_x[kXsOrderWarps][32], use_a[kXsOrderWarps][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = static_cast<int64_t>(blockIdx.x) * kXsOrderWarps + w;
@@ -829,16 +856,18 @@ __global__ void __launch_bounds__(32 * kXsOrderWarps) xs_order_kernel(
   if (__any_sync(0xffffffffu, cut)) return;
   // this lane's run: its entries' sorted positions and banks
   int32_t mine_i[32];
-  uint8_t mine_x[32], mine_a[32];
+  uint16_t mine_k[32];  // the accumulator within the cell: bank << 10 | accumulator / 32
+  uint8_t mine_x[32];
   int m = 0;
   for (int64_t i = u0; i < u0 + n; ++i) {
     if (((outpos[i] - st) & 31) != lane) continue;
     mine_i[m] = static_cast<int32_t>(i - u0);
     mine_x[m] = static_cast<uint8_t>(col[vals[i]] & 31);
-    mine_a[m] = static_cast<uint8_t>((keys[i] >> 10) & 31u);
+    mine_k[m] = static_cast<uint16_t>(keys[i] & 0x7FFFu);
     ++m;
   }
   uint32_t taken = 0;
+  int last = -1;  // the accumulator of the lane's previous pick
   __syncwarp();
   for (int s = 0; s < S; ++s) {
     use_x[w][lane] = 0;
@@ -849,7 +878,9 @@ __global__ void __launch_bounds__(32 * kXsOrderWarps) xs_order_kernel(
         int best = -1, best_cost = 1 << 30;
         for (int t = 0; t < m; ++t) {
           if ((taken >> t) & 1u) continue;
-          const int cost = use_x[w][mine_x[t]] + use_a[w][mine_a[t]];
+          const bool cont = cont_runs && s % G != 0 && mine_k[t] == last;
+          const int cost = cont_runs ? use_x[w][mine_x[t]] + (cont ? 0 : 2 * (1 + use_a[w][mine_k[t] >> 10]))
+                                     : use_x[w][mine_x[t]] + use_a[w][mine_k[t] >> 10];
           if (cost < best_cost) {
             best_cost = cost;
             best = t;
@@ -857,11 +888,31 @@ __global__ void __launch_bounds__(32 * kXsOrderWarps) xs_order_kernel(
         }
         taken |= 1u << best;
         ++use_x[w][mine_x[best]];
-        ++use_a[w][mine_a[best]];
+        if (!(cont_runs && s % G != 0 && mine_k[best] == last)) ++use_a[w][mine_k[best] >> 10];
+        last = mine_k[best];
         outpos[u0 + mine_i[best]] = st + 32 * s + lane;
       }
       __syncwarp();
     }
+  }
+}
+
+// One warp per cell: lane l marks the entries of its run that continue the
+// accumulator of its previous step inside the same register group of G steps
+// (kXsCont), so that the kernel keeps the running sum in a register there.
+__global__ void xs_cont_kernel(const int32_t* __restrict__ seg, const int32_t* __restrict__ counts, int64_t cells,
+                               int G, uint32_t* __restrict__ idx) {
+  const int64_t c = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= cells || counts[c] == 0) return;
+  const int32_t st = seg[c], S = seg[cells + c], fp = seg[2 * cells + c];
+  const XsLayout lay = xs_layout(S, fp, lane);
+  uint32_t prev = 0;
+  for (int32_t s = 0; s < lay.mine; ++s) {
+    const int64_t pos = static_cast<int64_t>(st) + static_cast<int64_t>(s) * lay.F + (s < lay.P ? s : lay.P) + lane;
+    const uint32_t v = idx[pos];
+    if (s % G != 0 && (v >> kXsColBits) == (prev >> kXsColBits)) idx[pos] = v | kXsCont;
+    prev = v;
   }
 }
 
@@ -1247,7 +1298,7 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool force_pair, 
   }
   const int64_t matrix_bytes = Z * (vb + 4);
   const int64_t x_bytes = static_cast<int64_t>(tl_slice.size()) * sizeof(VT) * SC;
-  if (!force && x_bytes > 4 * matrix_bytes) return MAXE_OK;  // the CSR kernel will do better
+  if (!force && x_bytes > 8 * matrix_bytes) return MAXE_OK;  // the CSR kernel will do better
   if (Zp + kXsSlack > INT32_MAX) return MAXE_OK;
   // ---- the format's arrays
   uint32_t* idx = owned.get<uint32_t>(Zp + kXsSlack);
@@ -1270,10 +1321,12 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool force_pair, 
                                                                               cells, G, outpos);
   MAXE_CUDA_TRY(cudaGetLastError());
   xs_order_kernel<<<static_cast<unsigned>(ceil_div(cells, kXsOrderWarps)), 32 * kXsOrderWarps, 0, st>>>(
-      keys, vals, h->col, d_ustart, counts, d_seg, cells, outpos);
+      keys, vals, h->col, d_ustart, counts, d_seg, cells, G, sizeof(VT) == 8, outpos);
   MAXE_CUDA_TRY(cudaGetLastError());
   xs_scatter_kernel<<<static_cast<unsigned>(ceil_div(Z, 256)), 256, 0, st>>>(keys, vals, Z, outpos, h->col, h->val,
                                                                              vb, SC, nS, idx, xval);
+  MAXE_CUDA_TRY(cudaGetLastError());
+  xs_cont_kernel<<<static_cast<unsigned>(ceil_div(cells * 32, 256)), 256, 0, st>>>(d_seg, counts, cells, G, idx);
   MAXE_CUDA_TRY(cudaGetLastError());
   MAXE_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors and scratch go out of scope
   owned.keep();

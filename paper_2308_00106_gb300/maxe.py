@@ -33,6 +33,7 @@ MAXE_COO = 0x40
 MAXE_XSLICE = 0x80
 MAXE_XS_PAIRS = 0x100
 MAXE_XS_SINGLE = 0x200
+MAXE_SPMM_ROWS = 0x400
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -45,7 +46,7 @@ EXPORTS = [
     "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
     "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather", "maxe_entropy_levels",
     "maxe_nnz_histogram", "maxe_gradient_permutation", "maxe_coo_spmv", "maxe_handle_coo",
-    "maxe_power_iteration_history", "maxe_set_wait_limit_ns", "maxe_selftest_wait",
+    "maxe_power_iteration_history", "maxe_set_wait_limit_ns", "maxe_selftest_wait", "maxe_batch_plan_shape",
 ]
 MAXE_BATCH_SCATTER_Y = 0x1
 
@@ -137,6 +138,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_batch_destroy": [P],
             "maxe_batch_tune": [P, I32, P],
             "maxe_batch_plan_info": [P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32)],
+            "maxe_batch_plan_shape": [P, ctypes.POINTER(I32)],
             "maxe_vec_norm_gather": [P, I32, I32, P, P, P, P],
             "maxe_entropy_levels": [P, I32, I32, I32, ctypes.c_double, P, P],
             "maxe_nnz_histogram": [P, I32, P, P],
@@ -252,6 +254,10 @@ class Handle:
         """True when the x-sliced SpMV runs each tile on a cluster of two CTAs (column halves)."""
         return bool(self._tuning() & 0x800)
 
+    def spmm_rows(self) -> bool:
+        """True when SpMM takes one row per group of lanes (MAXE_SPMM_ROWS, or kept by the autotuner)."""
+        return bool(self._tuning() & 0x1000)
+
     def spmm_lanes(self) -> bool:
         """True when SpMM spreads the k columns across lanes (else column passes)."""
         return bool(self._tuning() & 0x100)
@@ -316,7 +322,7 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
                      stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False,
                      equal_rows: bool = False, coo: bool = False, xslice: bool = False,
-                     xs_pairs: bool | None = None) -> Handle:
+                     xs_pairs: bool | None = None, spmm_rows: bool = False) -> Handle:
     """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity.
     xs_pairs: None lets the library decide whether the x-sliced form runs its
     tiles on CTA pairs (column halves); True / False forces it on / off."""
@@ -334,7 +340,8 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
     flags = ((MAXE_VALIDATE if validate else 0) | (MAXE_AUTOTUNE if autotune else 0) | (MAXE_ITEMS16 if items16 else 0)
              | (MAXE_SPMM_LANES if spmm_lanes else 0) | (MAXE_EQUAL_ROWS if equal_rows else 0)
              | (MAXE_COO if coo else 0) | (MAXE_XSLICE if xslice else 0)
-             | (0 if xs_pairs is None else (MAXE_XS_PAIRS if xs_pairs else MAXE_XS_SINGLE)))
+             | (0 if xs_pairs is None else (MAXE_XS_PAIRS if xs_pairs else MAXE_XS_SINGLE))
+             | (MAXE_SPMM_ROWS if spmm_rows else 0))
     _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
@@ -428,10 +435,10 @@ def maxe_version() -> str:
 
 
 def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False,
-             spmm_lanes=False, equal_rows=False, coo=False, xslice=False, xs_pairs=None) -> Handle:
+             spmm_lanes=False, equal_rows=False, coo=False, xslice=False, xs_pairs=None, spmm_rows=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
     return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16,
-                            spmm_lanes, equal_rows, coo, xslice, xs_pairs)
+                            spmm_lanes, equal_rows, coo, xslice, xs_pairs, spmm_rows)
 
 
 class Batch:
@@ -490,6 +497,13 @@ def maxe_batch_plan_info(h: Handle):
     _check(load().maxe_batch_plan_info(ctypes.c_void_p(h.ptr), ctypes.byref(H), ctypes.byref(t), ctypes.byref(it)),
            "maxe_batch_plan_info")
     return H.value, t.value, it.value
+
+
+def maxe_batch_plan_shape(h: Handle) -> int:
+    """CTAs per SM the handle's batch plan asks of a launch (0: as many as fit)."""
+    v = ctypes.c_int32()
+    _check(load().maxe_batch_plan_shape(ctypes.c_void_p(h.ptr), ctypes.byref(v)), "maxe_batch_plan_shape")
+    return v.value
 
 
 def maxe_vec_norm_gather(Q: torch.Tensor | None, w: torch.Tensor, u: torch.Tensor, scratch: torch.Tensor, stream=None):

@@ -108,3 +108,24 @@ def check_all_rows(y, rp, co, va, dtype: str, x, what=""):
     if dtype == "bf16":
         assert err <= BF16_TIGHT, (what, err)
     return err
+
+
+def check_all_rows_spmm(Y, rp, co, va, dtype: str, X, what=""):
+    """check_all_rows for Y = A X with k columns (every row and column), from
+    the oracle's SpMM of A X and of |A| |X|."""
+    Y = np.asarray(Y, dtype=np.float64)
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+    if X.ndim == 1:
+        return check_all_rows(Y, rp, co, va, dtype, X, what)
+    M = len(rp) - 1
+    ref = oracle.spmm(M, rp, co, va, code(dtype), X)
+    mag = oracle.spmm(M, rp, co, abs_values(va, dtype), code(dtype), np.abs(X))
+    n = np.diff(np.asarray(rp, dtype=np.int64))[:, None]
+    bound = (2 * n + 2) * UNIT[dtype] * mag * 1.01
+    bad = np.abs(Y - ref) > bound
+    assert not bad.any(), (what, int(bad.sum()), np.unravel_index(int(np.argmax(bad)), bad.shape))
+    err = rel_l2(Y, ref)
+    assert err <= TOL[dtype], (what, err)
+    if dtype == "bf16":
+        assert err <= BF16_TIGHT, (what, err)
+    return err

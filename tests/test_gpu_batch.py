@@ -113,6 +113,41 @@ def test_batch_tune_keeps_results():
         _check_against_oracle(A_, r, c, X, Y, False)
 
 
+@pytest.mark.parametrize("k", [1, 8])
+def test_batch_tune_is_never_slower_than_the_default_plan(k):
+    """Two handles of one matrix, one with the default batch plan and one tuned:
+    a batch of copies of the tuned item takes no longer than the same batch of
+    the default item (5% timing margin); the tuned plan keeps the product."""
+    A = W.poisson_uniform(4, 120000, 24.0, "f32")
+    (A_, hd, r, c, X), = _setup([A], [k], seed=4)
+    ht = maxe.from_csr(A_.to("cuda"), r, c)
+    maxe.maxe_batch_tune(ht, k)
+    assert maxe.maxe_batch_plan_shape(ht) >= 0
+
+    def batch_ms(h, copies=16, reps=5):
+        Y = torch.empty((A.rows, X.shape[1]), dtype=X.dtype, device="cuda")
+        b = maxe.Batch(copies)
+        b.set([(h, X, Y, False)] * copies)
+        for _ in range(3):
+            b.run()
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                b.run()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        b.close()
+        return best, Y
+
+    t_def, _ = batch_ms(hd)
+    t_tuned, Y = batch_ms(ht)
+    assert t_tuned <= 1.05 * t_def, (t_tuned, t_def, maxe.maxe_batch_plan_info(ht))
+    _check_against_oracle(A_, r, c, X, Y, False)
+
+
 def test_batch_run_in_cuda_graph():
     mats = [W.poisson_uniform(60 + i, 20000 + 7000 * i, 12.0, "f32") for i in range(5)]
     items = _setup(mats, [1, 4, 2, 16, 3], seed=11)

@@ -1,8 +1,9 @@
 """Parity at the full sizes the benchmark runs, in the launch configuration it
-times (autotuned handles; vectors in the permuted space), on outputs sampled
-row by row from the FP64 oracle: the 1M-row power-law matrix, the 5-point
-Laplacian on a 4096 x 4096 grid in all three value types with k = 1, 4, 16,
-and the 256-matrix batch in one persistent launch."""
+times (autotuned handles; vectors in the permuted space), on every row and
+column against the FP64 oracle (relative L2 and a per-row rounding bound):
+the 1M-row power-law matrix in all three value types, permuted and plain, the
+5-point Laplacian on a 4096 x 4096 grid in all three value types with
+k = 1, 4, 16, and the 256-matrix batch in one persistent launch."""
 import numpy as np
 import pytest
 import torch
@@ -10,7 +11,7 @@ import torch
 import oracle
 from paper_2308_00106_gb300 import maxe
 from paper_2308_00106_gb300 import workloads as W
-from tests.gpu_common import TOL, code, rel_l2
+from tests.gpu_common import check_all_rows, check_all_rows_spmm
 
 pytestmark = pytest.mark.gpu
 
@@ -28,37 +29,32 @@ def _vals_np(val: torch.Tensor):
     return v.view(torch.int16).numpy().view(np.uint16) if v.dtype == torch.bfloat16 else v.numpy()
 
 
-def _sampled(h, X, Y, dtype, rows, cols=None):
-    """Y[rows, c] against the oracle on the handle's own (permuted) CSR."""
+def _all(h, X, Y, dtype, what=""):
+    """Y = A' X (every row and column) against the oracle on the handle's own CSR."""
     rp, co, va, _, _ = h.csr()
-    rp, co, va = rp.cpu().numpy(), co.cpu().numpy(), _vals_np(va)
-    Xc = X.cpu().double().numpy()
-    Yc = Y.cpu().double().numpy()
-    if Xc.ndim == 1:
-        Xc, Yc = Xc[:, None], Yc[:, None]
-    for c in (range(Xc.shape[1]) if cols is None else cols):
-        ref = oracle.spmv_rows(rp, co, va, code(dtype), np.ascontiguousarray(Xc[:, c]), rows)
-        assert rel_l2(Yc[rows, c], ref) <= TOL[dtype], (dtype, c)
+    check_all_rows_spmm(Y.cpu().numpy(), rp.cpu().numpy(), co.cpu().numpy(), _vals_np(va), dtype,
+                        X.cpu().numpy(), what)
 
 
-def test_powerlaw_1M_full_size_as_benchmarked():
-    A = W.powerlaw(2308, device="cuda")
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
+def test_powerlaw_1M_full_size_as_benchmarked(dtype):
+    base = W.powerlaw(2308, device="cuda")
+    A = base if dtype == "f32" else base.astype(dtype)
     r = maxe.maxe_build_permutation(2308, A.rows, 0)
     c = maxe.maxe_build_permutation(2308, A.cols, 1)
-    rows = np.random.default_rng(0).choice(A.rows, 5000, replace=False)
+    vdt = "f64" if dtype == "f64" else "f32"
     for perms in ((r, c), (None, None)):
         h = maxe.from_csr(A, *perms, autotune=True)
-        x = W.vector(1, A.cols, "f32", "cuda")
+        x = W.vector(1, A.cols, vdt, "cuda")
         y = maxe.maxe_spmv(h, x, permuted=True)
-        _sampled(h, x, y, "f32", rows)
+        _all(h, x, y, dtype, ("permuted" if perms[0] is not None else "plain", h.xslice(), h.xslice_pairs()))
         h.close()
     # the original-space call: x gathered through cperm, y scattered through rperm
     h = maxe.from_csr(A, r, c, autotune=True)
-    x = W.vector(2, A.cols, "f32", "cuda")
+    x = W.vector(2, A.cols, vdt, "cuda")
     y = maxe.maxe_spmv(h, x)
     rp, co, va = A.numpy()
-    ref = oracle.spmv_rows(rp, co, va, code("f32"), x.cpu().numpy(), rows)
-    assert rel_l2(y.cpu().numpy()[rows], ref) <= TOL["f32"]
+    check_all_rows(y.cpu().numpy(), rp, co, va, dtype, x.cpu().numpy(), "original space")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
@@ -67,7 +63,6 @@ def test_laplacian_4096_full_size(dtype):
     A = base.astype(dtype)
     r = maxe.maxe_build_permutation(2308, A.rows, 0)
     c = maxe.maxe_build_permutation(2308, A.cols, 1)
-    rows = np.random.default_rng(1).choice(A.rows, 3000, replace=False)
     vdt = "f64" if dtype == "f64" else "f32"
     for perms in ((r, c), (None, None)):
         h = maxe.from_csr(A, *perms, autotune=True)
@@ -78,7 +73,7 @@ def test_laplacian_4096_full_size(dtype):
             else:
                 X = W.matrix_rhs(k, A.cols, k, vdt, "cuda")
                 Y = maxe.maxe_spmm(h, X, permuted=True)
-            _sampled(h, X, Y, dtype, rows, cols=None if k == 1 else (0, k // 2, k - 1))
+            _all(h, X, Y, dtype, (k, perms[0] is not None, h.spmm_rows(), h.spmm_lanes()))
             del X, Y
         h.close()
 
@@ -99,11 +94,8 @@ def test_batched_256_full_size_one_launch():
     b.set([(h, X, Y, False) for h, X, Y in zip(hs, Xs, Ys)])
     b.run()
     torch.cuda.synchronize()
-    g = np.random.default_rng(2)
-    for m in g.choice(len(mats), 12, replace=False):
-        A = mats[m]
-        rows = g.choice(A.rows, min(A.rows, 500), replace=False)
-        _sampled(hs[m], Xs[m], Ys[m], "f32", rows, cols=sorted({0, ks[m] - 1}))
+    for m in range(len(mats)):
+        _all(hs[m], Xs[m], Ys[m], "f32", ("batch item", m, ks[m]))
     b.close()
     for h in hs:
         h.close()
