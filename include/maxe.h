@@ -63,10 +63,11 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * are in range and perms are bijections (synchronises; MAXE_ERR_INVALID on failure). */
 #define MAXE_VALIDATE 0x2u
 /* Flag of maxe_permute_csr: time the SpMV kernel variants (8 or 16 entries
- * per lane) on this matrix and keep the faster one for the handle; also time
- * the two SpMM paths (column passes, or columns across lanes) at k = 16 when
- * their scratch (rows + cols) * 16 vectors fits in 3 GiB, and keep the faster
- * (synchronises; a few products of device time). */
+ * per lane) on this matrix and keep the faster one for the handle, the same
+ * for the x-sliced form when the handle has one; also time the three SpMM
+ * paths (column passes, columns across lanes, one row per lane group) at
+ * k = 16 when their scratch (rows + cols) * 16 vectors fits in 8 GiB, and keep
+ * the fastest (synchronises; a few products of device time). */
 #define MAXE_AUTOTUNE 0x4u
 /* Flag of maxe_permute_csr: use the 16-entries-per-lane SpMV variant without
  * timing (tuning override; MAXE_AUTOTUNE takes precedence). */

@@ -245,7 +245,7 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st) {
   // SpMM path for wide right-hand sides, timed at k = 16 when the scratch is modest
   const int64_t k = 16;
   const int64_t bytes = (static_cast<int64_t>(h->rows) + h->cols) * k * eb;
-  if (s == MAXE_OK && bytes <= (int64_t(3) << 30)) {
+  if (s == MAXE_OK && bytes <= (int64_t(8) << 30)) {
     void* X = h->al.get(static_cast<size_t>(h->cols) * k * eb);
     void* Y = h->al.get(static_cast<size_t>(h->rows) * k * eb);
     if (X && Y) {
@@ -253,10 +253,12 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st) {
       float t_pass = 0.f, t_lc = 0.f, t_rows = 0.f;
       if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 0); }, &t_pass);
       if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 1); }, &t_lc);
-      if (s == MAXE_OK) s = timed([&] { return spmm_rows_launch(h, k, X, k, Y, k, nullptr, st); }, &t_rows);
+      const bool rows_ok = spmm_rows_ready(h, static_cast<int32_t>(k), X, k, Y, k);
+      if (s == MAXE_OK && rows_ok)
+        s = timed([&] { return spmm_rows_launch(h, k, X, k, Y, k, nullptr, st); }, &t_rows);
       if (s == MAXE_OK) {
         h->spmm_lc = t_lc < t_pass ? 1 : 0;
-        h->spmm_rows = t_rows < std::min(t_pass, t_lc) ? 1 : 0;
+        h->spmm_rows = rows_ok && t_rows < std::min(t_pass, t_lc) ? 1 : 0;
       }
     }
     h->al.put(Y);
