@@ -92,7 +92,8 @@ def record_profile(csv_path: str, kernel: str, launch: int, command: str, worklo
     cols, units = rows[head], rows[head + 1]
     data = [r for r in rows[head + 2:] if len(r) == len(cols) and kernel in r[cols.index("Kernel Name")]]
     r = data[launch]
-    scale = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "nsecond": 1, "usecond": 1e3, "msecond": 1e6}
+    scale = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "nsecond": 1, "usecond": 1e3, "msecond": 1e6,
+             "ns": 1, "us": 1e3, "ms": 1e6}
 
     def val(name):
         i = cols.index(name)

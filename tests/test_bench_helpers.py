@@ -47,3 +47,15 @@ def test_traffic_records_are_tied_to_the_kernel_sources(kernel, tmp_path):
 def test_host_record():
     h = bench.host_info()
     assert h["nproc"] >= 1 and h["machine"]
+
+
+def test_headline_kernel_record_matches_its_sources():
+    # The roofline's traffic for the headline kernel comes from this record; a
+    # change to the kernel's sources must come with a new ncu capture.
+    p = os.path.join(ROOT, "profiles", bench.PROFILE_RECORD["spmv_xslice_kernel"])
+    assert os.path.exists(p), "no ncu record of spmv_xslice_kernel under profiles/"
+    rec = json.load(open(p))
+    assert rec["source_sha256"] == bench.kernel_source_hash("spmv_xslice_kernel"), \
+        "xslice.cu or internal.cuh changed since the ncu record was taken: capture and record it again"
+    alg = bench.alg_bytes(1 << 20, 1 << 20, 25394653, 4, 4, 4)
+    assert 0.9 * alg < rec["traffic_bytes_per_launch"] < 3 * alg
