@@ -473,7 +473,9 @@ def batched_measure(seed, count, steps, warmup, world, tune, profile=False):
     for m, (A, k) in enumerate(zip(mats, ks)):
         r = maxe.maxe_build_permutation(seed + m, A.rows, 0)
         c = maxe.maxe_build_permutation(seed + m, A.cols, 1)
-        h = maxe.from_csr(A, r, c)
+        # the per-matrix launches and the default batch plan take the same SpMM
+        # kernel (one row per lane group)
+        h = maxe.from_csr(A, r, c, spmm_rows=True)
         if tune:
             maxe.maxe_batch_tune(h, k)
         hs.append(h)
@@ -506,6 +508,10 @@ def batched_measure(seed, count, steps, warmup, world, tune, profile=False):
     ms_pm_graph, _ = timed_steps(step_permatrix, K, warmup, world, graph_len=1 if K < 2 else 2)
     ms_pm, _ = timed_steps(step_permatrix, K, warmup, world, graph_len=1)
     plans = [maxe.maxe_batch_plan_info(h) for h in hs]
+    kernels = ["spmv16" if k == 1 and p[2] == 16 else "spmv8" if k == 1 else h.batch_spmm_kernel()
+               for h, k, p in zip(hs, ks, plans)]
+    # one persistent launch per kernel class present (the SpMM passes and lanes kernels share one)
+    launches = len({"spmm" if kn in ("passes", "lanes") else kn for kn in kernels})
     hbm, src = peaks()
     gbs = total / (ms_b * 1e-3) / 1e9
     b.close()
@@ -526,8 +532,9 @@ def batched_measure(seed, count, steps, warmup, world, tune, profile=False):
         "roofline": {"bound": "hbm", "achieved": round(gbs, 3), "peak": hbm, "unit": "GB/s",
                      "frac": round(gbs / hbm, 4), "peak_source": src},
         "plans": {"entries_per_task": sorted({p[0] for p in plans})[:8],
-                  "items16": sum(1 for p in plans if p[2] == 16), "tuned": bool(tune)},
-        "gen_s": t_gen, "prep_and_tune_s": t_prep, "gpu_launches_per_batch": 1,
+                  "items16": sum(1 for p in plans if p[2] == 16), "tuned": bool(tune),
+                  "kernels": {kn: kernels.count(kn) for kn in sorted(set(kernels))}},
+        "gen_s": t_gen, "prep_and_tune_s": t_prep, "gpu_launches_per_batch": launches,
     }
 
 

@@ -219,7 +219,9 @@ MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, c
  * SpMV uses the x-sliced form (MAXE_XSLICE), plus 0x400 when that form's cells
  * are large enough for its L2 prefetch cursor, plus 0x800 when it runs its tiles
  * on pairs of CTAs (column halves), plus 0x1000 when SpMM takes one row per
- * group of lanes (MAXE_SPMM_ROWS).  items: (host). */
+ * group of lanes (MAXE_SPMM_ROWS), plus the SpMM kernel of the batch plan in
+ * bits 13-14 (0 column passes, 1 columns across lanes, 2 one row per lane
+ * group).  items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;
@@ -300,14 +302,19 @@ MAXE_API maxe_status maxe_spmm(const maxe_handle* h, int32_t k, const void* X, i
 
 /* a9.  Batched persistent SpMV/SpMM (many uneven matrices, each with its own
  * k right-hand sides, in one persistent launch per value type and kernel
- * class present: unit-stride SpMV with 8 or with 16 entries per lane, or SpMM).
+ * class present: unit-stride SpMV with 8 or with 16 entries per lane, SpMM by
+ * column passes or columns across lanes, or SpMM with one row per lane group
+ * for items whose X and Y rows are 16-byte aligned (ldx and ldy multiples of
+ * 16 bytes / element size) -- the class maxe_spmm's MAXE_SPMM_ROWS path runs).
  *
  * An item asks for Y = A' X on a handle: X (device) is in the permuted space
  * (x' = x[cperm], rows of X gathered), row-major cols x k with leading
  * dimension ldx >= k; Y (device) rows x k, ldy >= k, written in the permuted
  * space, or through rperm into the original space with MAXE_BATCH_SCATTER_Y.
- * 1 <= k <= 64.  Each handle carries a batch plan (entries per warp task and
- * entries per lane), made at creation and retuned by maxe_batch_tune; it does
+ * 1 <= k <= 64.  Each handle carries a batch plan (entries per warp task,
+ * entries per lane and the SpMM kernel: the handle's own SpMM path when it was
+ * autotuned or set by a flag, else one row per lane group), made at creation
+ * and retuned by maxe_batch_tune; it does
  * not depend on the other items, so an item's result is bit-identical alone
  * and in any mix.
  *
@@ -342,8 +349,9 @@ MAXE_API maxe_status maxe_batch_destroy(maxe_batch* b);
  * warps once and four times over, are timed (the best of three timings each;
  * every plan on the same copies) for: the handle's current plan; entries per task
  * (rows per warp task) in {512, 2048, 8192, 32768} (at least nnz / resident
- * warps) x the kernel variant (8 or 16 entries per lane for k = 1, column
- * passes or columns across lanes for k > 1); then, for the best of those, the
+ * warps) x the kernel variant (8 or 16 entries per lane for k = 1; column
+ * passes, columns across lanes or one row per lane group for k > 1); then, for
+ * the best of those, the
  * CTA shape of the launch (fewer CTAs per SM than fit).  The current plan is
  * replaced only by one at least 3% faster at both fills, so tuning never keeps
  * a slower plan.  In a batch, a launch uses the largest CTA count per SM its items'

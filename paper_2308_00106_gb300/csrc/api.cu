@@ -218,7 +218,9 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (s == MAXE_OK && (flags & MAXE_SPMM_LANES)) h->spmm_lc = 1;
   if (s == MAXE_OK && (flags & MAXE_SPMM_ROWS)) h->spmm_rows = 1;
   if (s == MAXE_OK && (flags & MAXE_AUTOTUNE)) s = spmv_autotune(h, st);
-  if (s == MAXE_OK) h->blc = h->spmm_lc;  // the default batch plan follows the handle's SpMM path
+  // the default batch plan follows the handle's SpMM path where it was tuned
+  // or asked for, else takes the rows kernel
+  if (s == MAXE_OK) h->blc = h->spmm_rows ? 2 : (h->spmm_lc ? 1 : ((flags & MAXE_AUTOTUNE) ? 0 : 2));
   if (s != MAXE_OK) {
     release(h);
     return s;
@@ -245,7 +247,7 @@ maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
   if (!h || !items) return MAXE_ERR_INVALID;
   *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0) | (h->xs_use ? 0x200 : 0) |
            (h->xs_use && h->xs_prefetch ? 0x400 : 0) | (h->xs_use && h->xs_pair == 2 ? 0x800 : 0) |
-           (h->spmm_rows ? 0x1000 : 0);
+           (h->spmm_rows ? 0x1000 : 0) | ((h->blc & 3) << 13);
   return MAXE_OK;
 }
 

@@ -22,6 +22,7 @@
 #include <new>
 #include <vector>
 
+#include "spmm_rows.cuh"
 #include "spmv_warp.cuh"
 
 namespace maxe {
@@ -54,8 +55,9 @@ struct BatchParams {
 // class is its own persistent kernel (one launch per value type and class
 // present in a batch): 0 = plain SpMV (k = 1, unit strides), 8 entries per
 // lane; 1 = the same with 16 entries per lane; 2 = SpMM (1, 2 or 4 columns per
-// pass, any strides).
-constexpr int kClasses = 3;
+// pass, or columns across lanes, any strides); 3 = SpMM with one row per lane
+// group (spmm_rows.cuh: 16-byte aligned X and Y rows).
+constexpr int kClasses = 4;
 
 template <typename VT, int CLASS>
 struct BatchClass {
@@ -69,6 +71,7 @@ struct BatchClass {
       m = std::max(m, sizeof(WarpSmemLC<VT>));
       if (sizeof(typename Acc<VT>::T) == 4) m = std::max(m, sizeof(WarpSmem<VT, 4, 8>));
     }
+    if (CLASS == 3) m = sizeof(rows::RowsStage<VT>);
     return (m + 127) & ~size_t(127);
   }
 };
@@ -128,8 +131,42 @@ __global__ void __launch_bounds__(kThreads, BatchClass<VT, CLASS>::kMinBlocks) s
   }
 }
 
-// class of an item (see above)
-int item_class(int vw, int unit, int it16) { return unit ? (it16 ? 1 : 0) : 2; }
+// Class 3: each warp task (item, warp range of the item's batch plan) runs
+// the rows of its range through the chunk pipeline of spmm_rows.cuh, G lanes
+// per row as the item's k asks.
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) spmm_batch_rows_kernel(BatchParams bp) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  rows::RowsStage<VT>* s =
+      reinterpret_cast<rows::RowsStage<VT>*>(smem_raw + BatchClass<VT, 3>::warp_smem() * wib);
+  const int nwarps = gridDim.x * kWarps;
+  for (int t = blockIdx.x * kWarps + wib; t < bp.ntasks;) {
+    int lo = 0, hi = bp.nitems - 1;  // item of task t: last item with task0 <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bp.task0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const BatchItem& it = bp.items[lo];
+    const rows::RowsOperand op{it.rowptr, it.col, it.val, it.X, it.Y, it.yperm, it.ldx, it.ldy, it.k};
+    const int w = t - bp.task0[lo];
+    rows::rows_range<VT>(s, op, it.wrow[w], it.wrow[w + 1], rows::rows_group<VT>(it.k), lane);
+    int nt = 0;
+    if (lane == 0) nt = nwarps + atomicAdd(bp.next, 1);
+    t = __shfl_sync(0xffffffffu, nt, 0);
+  }
+}
+
+template <typename VT, int CLASS>
+constexpr auto batch_kernel() {
+  if constexpr (CLASS == 3)
+    return spmm_batch_rows_kernel<VT>;
+  else
+    return spmm_batch_kernel<VT, CLASS>;
+}
+
+// class of an item (see above); rows: the item takes the rows kernel
+int item_class(int vw, int unit, int it16, bool rows) { return unit ? (it16 ? 1 : 0) : (rows ? 3 : 2); }
 
 template <typename VT, int CLASS>
 maxe_status batch_prepare(int* blocks_per_sm) {
@@ -140,10 +177,10 @@ maxe_status batch_prepare(int* blocks_per_sm) {
   if (dev < 0 || dev >= 64) return MAXE_ERR_UNSUPPORTED;
   MAXE_TRY(once.run([dev] {
     const size_t smem = BatchClass<VT, CLASS>::warp_smem() * kWarps;
-    MAXE_CUDA_TRY(cudaFuncSetAttribute(spmm_batch_kernel<VT, CLASS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    MAXE_CUDA_TRY(cudaFuncSetAttribute(batch_kernel<VT, CLASS>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem)));
     int o = 0;
-    MAXE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_batch_kernel<VT, CLASS>, kThreads, smem));
+    MAXE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, batch_kernel<VT, CLASS>(), kThreads, smem));
     occ[dev] = o > 0 ? o : 1;
     return MAXE_OK;
   }));
@@ -160,7 +197,7 @@ maxe_status batch_launch(const BatchParams& bp, int sms, int bps, cudaStream_t s
   if (bps > 0 && bps < occ) occ = bps;
   const int64_t want = ceil_div(bp.ntasks, kWarps);
   const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * occ)));
-  spmm_batch_kernel<VT, CLASS><<<grid, kThreads, BatchClass<VT, CLASS>::warp_smem() * kWarps, st>>>(bp);
+  batch_kernel<VT, CLASS>()<<<grid, kThreads, BatchClass<VT, CLASS>::warp_smem() * kWarps, st>>>(bp);
   MAXE_CUDA_TRY(cudaGetLastError());
   return MAXE_OK;
 }
@@ -169,7 +206,8 @@ template <typename VT>
 maxe_status batch_launch_class(int cls, const BatchParams& bp, int sms, int bps, cudaStream_t st) {
   if (cls == 0) return batch_launch<VT, 0>(bp, sms, bps, st);
   if (cls == 1) return batch_launch<VT, 1>(bp, sms, bps, st);
-  return batch_launch<VT, 2>(bp, sms, bps, st);
+  if (cls == 2) return batch_launch<VT, 2>(bp, sms, bps, st);
+  return batch_launch<VT, 3>(bp, sms, bps, st);
 }
 
 maxe_status launch_for(maxe_dtype d, int cls, const BatchParams& bp, int sms, int bps, cudaStream_t st) {
@@ -189,7 +227,8 @@ int batch_occupancy(maxe_dtype d, int cls) {
     using VT = decltype(vt);
     if (cls == 0) s = batch_prepare<VT, 0>(&occ);
     else if (cls == 1) s = batch_prepare<VT, 1>(&occ);
-    else s = batch_prepare<VT, 2>(&occ);
+    else if (cls == 2) s = batch_prepare<VT, 2>(&occ);
+    else s = batch_prepare<VT, 3>(&occ);
   };
   switch (d) {
     case MAXE_F64: one(double{}); break;
@@ -251,7 +290,7 @@ maxe_status batch_plan(maxe_handle* h, int64_t H, int it16, cudaStream_t st, int
 maxe_status batch_plan_default(maxe_handle* h, cudaStream_t st) {
   const int64_t target = batch_resident_warps(h->dtype, h->sms);
   return batch_plan(h, std::max<int64_t>(kDefaultBatchTask, ceil_div(std::max<int64_t>(h->nnz, 1), target)), 0, st,
-                    0);
+                    2);
 }
 
 }  // namespace maxe
@@ -373,7 +412,8 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
       const int vw = pick_vw(a, eb);
       const int unit = (a.k == 1 && a.ldx == 1 && a.ldy == 1) ? 1 : 0;
       const int it16 = (unit && h->bit16) ? 1 : 0;
-      if (item_class(vw, unit, it16) != cls) continue;
+      const bool rows = !unit && h->blc == 2 && spmm_rows_ready(h, a.k, a.X, a.ldx, a.Y, a.ldy);
+      if (item_class(vw, unit, it16, rows) != cls) continue;
       BatchItem& d = hi[m];
       d.rowptr = h->rowptr;
       d.col = h->col;
@@ -390,7 +430,7 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
       d.vw = vw;
       d.unit = unit;
       d.it16 = it16;
-      d.lcg = (unit || !h->blc) ? 0 : lc_group(a.k, eb, static_cast<int>(a.ldx % 1024), static_cast<int>(a.ldy % 1024));
+      d.lcg = (unit || h->blc != 1) ? 0 : lc_group(a.k, eb, static_cast<int>(a.ldx % 1024), static_cast<int>(a.ldy % 1024));
       if (d.lcg > 0 && vw < (eb == 4 ? 4 : 2)) d.lcg = 0;  // needs 16-byte aligned X and Y rows
       ht[m] = static_cast<int32_t>(tasks);
       tasks += h->bnW;
@@ -495,10 +535,12 @@ maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
                              std::max<int64_t>(8192, floor_h), std::max<int64_t>(32768, floor_h)};
   for (int ci = 0; ci < 4 && s == MAXE_OK; ++ci) {
     if (ci > 0 && cand_h[ci] == cand_h[ci - 1]) continue;
-    for (int var = 0; var <= 1 && s == MAXE_OK; ++var) {
-      // second variant: 16 entries per lane for k = 1, columns across lanes for k > 1
+    for (int var = 0; var <= (k == 1 ? 1 : 2) && s == MAXE_OK; ++var) {
+      // k = 1: 8 or 16 entries per lane; k > 1: column passes, columns across
+      // lanes, one row per lane group
       const Plan pl{cand_h[ci], (k == 1) ? var : 0, (k > 1) ? var : 0, 0};
       if (var == 1 && k > 1 && lc_group(k, eb, kp % 1024, kp % 1024) == 0) continue;
+      if (var == 2 && !spmm_rows_ready(h, k, X, kp, Y, kp)) continue;
       if (pl.H == current.H && pl.it16 == current.it16 && pl.lc == current.lc && pl.bps == current.bps) continue;
       float t1 = 0.f, t4 = 0.f;
       s = time_plan(pl, &t1, &t4);
@@ -509,7 +551,7 @@ maxe_status maxe_batch_tune(maxe_handle* h, int32_t k, void* stream) {
     }
   }
   // 2) CTAs per SM (the CTA shape of the launch) for the best of those
-  const int cls = (k == 1) ? (best.it16 ? 1 : 0) : 2;
+  const int cls = (k == 1) ? (best.it16 ? 1 : 0) : (best.lc == 2 ? 3 : 2);
   const int occ = batch_occupancy(h->dtype, cls);
   const Plan base = best;
   for (int bps = occ - 1; bps >= 1 && s == MAXE_OK; --bps) {

@@ -35,7 +35,7 @@ struct maxe_handle {
   int32_t bnW = 0;
   int64_t bH = 0;
   int bit16 = 0;                           // batch plan: 16 entries per lane for k = 1
-  int blc = 0;                             // batch plan: SpMM with columns across lanes
+  int blc = 0;                             // batch plan, SpMM: 0 column passes, 1 columns across lanes, 2 rows
   int bbps = 0;                            // batch plan: CTAs per SM of its launch (0: as many as fit)
   // x-sliced SpMV form (MAXE_XSLICE): entries grouped by ((tile, half, warp range), column slice)
   uint32_t* xs_idx = nullptr;              // (accumulator << 15) | column in slice, step-major cells

@@ -83,7 +83,7 @@ template <>
 struct XsCfg<float, 2> {
   static constexpr int kSliceCols = 12288;  // 48 KB
   static constexpr int kBuffers = 3;
-  static constexpr int kSteps = 12;
+  static constexpr int kSteps = 10;
 };
 template <>
 struct XsCfg<double, 1> {
@@ -167,6 +167,7 @@ struct XsVal<double> {  // FP64 values
   static __device__ __forceinline__ double ld(const void* v, int64_t e) {
     return __ldcs(static_cast<const double*>(v) + e);
   }
+  static __device__ __forceinline__ double raw(const void* v, int64_t e) { return ld(v, e); }
 };
 template <>
 struct XsVal<float> {  // FP32 values
@@ -174,6 +175,7 @@ struct XsVal<float> {  // FP32 values
   static __device__ __forceinline__ float ld(const void* v, int64_t e) {
     return __ldcs(static_cast<const float*>(v) + e);
   }
+  static __device__ __forceinline__ float raw(const void* v, int64_t e) { return ld(v, e); }
 };
 template <>
 struct XsVal<uint16_t> {  // BF16 values, FP32 arithmetic
@@ -181,15 +183,33 @@ struct XsVal<uint16_t> {  // BF16 values, FP32 arithmetic
   static __device__ __forceinline__ float ld(const void* v, int64_t e) {
     return __uint_as_float(static_cast<uint32_t>(__ldcs(static_cast<const unsigned short*>(v) + e)) << 16);
   }
+  static __device__ __forceinline__ uint16_t raw(const void* v, int64_t e) {
+    return __ldcs(static_cast<const unsigned short*>(v) + e);
+  }
 };
 
 // A group of up to G consecutive steps of a cell, in registers; ns = the
-// lane's steps in the group.
-template <typename AT, int G>
+// lane's steps in the group.  set(j, v) keeps step j's stored value, av(j)
+// gives it in the arithmetic type.
+template <typename ValT, int G>
 struct XsGroup {
+  using AT = typename XsVal<ValT>::AT;
   uint32_t id[G];
   AT a[G];
   int ns;
+  __device__ __forceinline__ void set(int j, ValT v) { a[j] = static_cast<AT>(v); }
+  __device__ __forceinline__ AT av(int j) const { return a[j]; }
+};
+// BF16: the raw 16-bit values, widened to FP32 only where the FMA uses them
+// -- widening at load time would make the load phase wait for each load.
+template <int G>
+struct XsGroup<uint16_t, G> {
+  using AT = float;
+  uint32_t id[G];
+  uint32_t a[G];
+  int ns;
+  __device__ __forceinline__ void set(int j, uint16_t v) { a[j] = v; }
+  __device__ __forceinline__ float av(int j) const { return __uint_as_float(a[j] << 16); }
 };
 
 // Position of a group in a warp's stream over its (tile, half)'s slices: slice
@@ -288,24 +308,9 @@ __device__ __forceinline__ auto xs_val_ptr(const void* v) {
     return static_cast<const ValT*>(v);
 }
 
-template <typename ValT>
-__device__ __forceinline__ typename XsVal<ValT>::AT xs_val_cvt(ValT v);
-template <>
-__device__ __forceinline__ double xs_val_cvt<double>(double v) {
-  return v;
-}
-template <>
-__device__ __forceinline__ float xs_val_cvt<float>(float v) {
-  return v;
-}
-template <>
-__device__ __forceinline__ float xs_val_cvt<uint16_t>(uint16_t v) {
-  return __uint_as_float(static_cast<uint32_t>(v) << 16);
-}
-
 template <typename ValT, int G>
 __device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int lane,
-                                        XsGroup<typename XsVal<ValT>::AT, G>& k) {
+                                        XsGroup<ValT, G>& k) {
   if (q.fp < 0) {  // full steps: step s at first + 32 s
     const int32_t mine = lane < (q.fp & 63) ? q.S : q.S - 1;
     const int32_t ns = mine - q.s0;
@@ -317,7 +322,7 @@ __device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int l
     for (int j = 0; j < G; ++j) {
       if (j < k.ns) {
         k.id[j] = __ldcs(pi + 32 * j);
-        k.a[j] = xs_val_cvt<ValT>(static_cast<ValT>(__ldcs(pv + 32 * j)));
+        k.set(j, static_cast<ValT>(__ldcs(pv + 32 * j)));
       }
     }
     return;
@@ -332,7 +337,7 @@ __device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int l
       const int32_t s = q.s0 + j;
       const int64_t pos = static_cast<int64_t>(q.st) + static_cast<int64_t>(s) * F + (s < P ? s : P) + lane;
       k.id[j] = __ldcs(p.idx + pos);
-      k.a[j] = XsVal<ValT>::ld(p.val, pos);
+      k.set(j, XsVal<ValT>::raw(p.val, pos));
     }
   }
 }
@@ -362,10 +367,11 @@ __device__ __forceinline__ void xs_prefetch(const XsParams& p, const XsPos& q, i
 // builder keeps them in different groups).  FP64: steps that continue the
 // previous step's accumulator (kXsCont) add into a register, the accumulator
 // is read at the first step of a run and written after its last (each FP64
-// accumulator access costs two shared-memory wavefronts, so this pays there;
-// in FP32 the per-lane branch costs more than the accesses it saves).
-template <typename VT, typename AT, int G>
-__device__ __forceinline__ void xs_compute(const XsGroup<AT, G>& k, const VT* __restrict__ xs, VT* acc) {
+// accumulator access costs two shared-memory wavefronts, so this pays there).
+// FP32: the group's reads, sums and writes go in three passes, so the reads
+// do not wait for the writes of earlier steps.
+template <typename VT, typename ValT, int G>
+__device__ __forceinline__ void xs_compute(const XsGroup<ValT, G>& k, const VT* __restrict__ xs, VT* acc) {
   VT xv[G];
 #pragma unroll
   for (int j = 0; j < G; ++j)
@@ -381,18 +387,30 @@ __device__ __forceinline__ void xs_compute(const XsGroup<AT, G>& k, const VT* __
           pa = acc + (k.id[j] >> kXsColBits);
           sum = *pa;
         }
-        sum = fma(static_cast<VT>(k.a[j]), xv[j], sum);
+        sum = fma(static_cast<VT>(k.av(j)), xv[j], sum);
       }
     }
     if (k.ns > 0) *pa = sum;
   } else {
+    // All of the group's accumulators are read first, then summed, then
+    // written in step order: within a group a lane's steps on one accumulator
+    // are consecutive (the builder keeps them so) and all but the first carry
+    // kXsCont, so they add to the running value instead of the stale read.
+    VT v[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j)
+      if (j < k.ns) v[j] = acc[k.id[j] >> kXsColBits];
+    VT run = VT(0);
 #pragma unroll
     for (int j = 0; j < G; ++j) {
       if (j < k.ns) {
-        VT* ap = acc + (k.id[j] >> kXsColBits);
-        *ap = fma(static_cast<VT>(k.a[j]), xv[j], *ap);
+        run = fma(static_cast<VT>(k.av(j)), xv[j], (j > 0 && (k.id[j] & kXsCont)) ? run : v[j]);
+        v[j] = run;
       }
     }
+#pragma unroll
+    for (int j = 0; j < G; ++j)
+      if (j < k.ns) acc[k.id[j] >> kXsColBits] = v[j];
   }
   __syncwarp();
 }
@@ -471,7 +489,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
     xs_window_load(p, g, i1, i0, lane, win);
     // Two register groups with fixed roles, A and B, summed in turn: while one
     // is summed the other's loads are in flight.
-    XsGroup<AT, G> kA, kB;
+    XsGroup<ValT, G> kA, kB;
     XsPos qA = xs_next_slice(p, g, i0 - 1, i1, lane, win);
     XsPos qB = xs_next<G>(p, g, qA, i1, lane, win);
     if (qA.i >= 0) xs_load<ValT, G>(p, qA, lane, kA);
@@ -506,7 +524,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
     };
     while (qA.i >= 0) {
       advance_to(qA.i);
-      if (ok) xs_compute<VT, AT, G>(kA, xb + ((v - 1) % NX) * SC, acc);
+      if (ok) xs_compute<VT, ValT, G>(kA, xb + ((v - 1) % NX) * SC, acc);
       qA = qn;
       if (qA.i >= 0) xs_load<ValT, G>(p, qA, lane, kA);
       qn = xs_next<G>(p, g, qn, i1, lane, win);
@@ -516,7 +534,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
       }
       if (qB.i < 0) break;
       advance_to(qB.i);
-      if (ok) xs_compute<VT, AT, G>(kB, xb + ((v - 1) % NX) * SC, acc);
+      if (ok) xs_compute<VT, ValT, G>(kB, xb + ((v - 1) % NX) * SC, acc);
       qB = qn;
       if (qB.i >= 0) xs_load<ValT, G>(p, qB, lane, kB);
       qn = xs_next<G>(p, g, qn, i1, lane, win);
@@ -826,7 +844,11 @@ __global__ void xs_pack_kernel(const uint64_t* __restrict__ keys, const int32_t*
 // One warp per packed cell of full steps (at most 32): the order of each run's
 // entries is free (an accumulator's entries are in one run), so it is chosen
 // step by step to spread the shared-memory banks a step touches: at step s the
-// lanes in turn take, among their remaining entries, the cheapest.  Without
+// lanes in turn take, among their remaining entries, the cheapest -- except
+// that inside a register group of G steps a lane continues its previous
+// accumulator while that has entries left, so that within a group each
+// accumulator of a lane occupies consecutive steps (the kernel reads all of a
+// group's accumulators before it writes any).  Without
 // register runs (FP32 kernels) the cost is how often the entry's x bank plus
 // its accumulator's bank are used at step s so far.  With register runs
 // (FP64: cont = true) an entry that continues the lane's previous accumulator
@@ -875,9 +897,15 @@ __global__ void __launch_bounds__(32 * kXsOrderWarps) xs_order_kernel(
     __syncwarp();
     for (int turn = 0; turn < 32; ++turn) {
       if (lane == turn && s < m) {
+        // inside a register group an accumulator's entries stay together: while
+        // the lane's previous accumulator has entries left, one of them is next
+        bool force = false;
+        if (s % G != 0)
+          for (int t = 0; t < m; ++t) force |= !((taken >> t) & 1u) && mine_k[t] == last;
         int best = -1, best_cost = 1 << 30;
         for (int t = 0; t < m; ++t) {
           if ((taken >> t) & 1u) continue;
+          if (force && mine_k[t] != last) continue;
           const bool cont = cont_runs && s % G != 0 && mine_k[t] == last;
           const int cost = cont_runs ? use_x[w][mine_x[t]] + (cont ? 0 : 2 * (1 + use_a[w][mine_k[t] >> 10]))
                                      : use_x[w][mine_x[t]] + use_a[w][mine_k[t] >> 10];

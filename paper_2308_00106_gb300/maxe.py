@@ -258,6 +258,10 @@ class Handle:
         """True when SpMM takes one row per group of lanes (MAXE_SPMM_ROWS, or kept by the autotuner)."""
         return bool(self._tuning() & 0x1000)
 
+    def batch_spmm_kernel(self) -> str:
+        """SpMM kernel of the handle's batch plan: "passes", "lanes" or "rows"."""
+        return ("passes", "lanes", "rows", "passes")[(self._tuning() >> 13) & 3]
+
     def spmm_lanes(self) -> bool:
         """True when SpMM spreads the k columns across lanes (else column passes)."""
         return bool(self._tuning() & 0x100)

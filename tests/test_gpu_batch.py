@@ -38,9 +38,12 @@ def _setup(mats, ks, seed=1):
     for i, (A, k) in enumerate(zip(mats, ks)):
         r = maxe.maxe_build_permutation(seed + i, A.rows, 0)
         c = maxe.maxe_build_permutation(seed + i, A.cols, 1)
-        # odd items use the columns-across-lanes SpMM path: one launch mixes both
-        h = maxe.from_csr(A.to("cuda"), r, c, spmm_lanes=bool(i % 2))
-        kp = (k + 3) // 4 * 4 if k > 1 else 1
+        # SpMM kernels of one mix: items 0, 3, ... one row per lane group (the
+        # default plan, X rows padded to 16 bytes); 1, 4, ... columns across
+        # lanes; 2, 5, ... unpadded X rows, which the rows kernel cannot take,
+        # so the default plan falls back to column passes
+        h = maxe.from_csr(A.to("cuda"), r, c, spmm_lanes=(i % 3 == 1))
+        kp = ((k + 3) // 4 * 4 if i % 3 != 2 else k) if k > 1 else 1
         Xb = torch.zeros(A.cols, kp, dtype=torch.float64 if A.dtype == "f64" else torch.float32, device="cuda")
         Xb[:, :k] = W.matrix_rhs(100 + i, A.cols, k, "f64" if A.dtype == "f64" else "f32", "cuda")
         items.append((A, h, r, c, Xb[:, :k]))
@@ -74,6 +77,14 @@ def test_batch_matches_oracle_per_item(scatter):
     torch.cuda.synchronize()
     for (A, h, r, c, X), Y in zip(items, Ys):
         _check_against_oracle(A, r, c, X, Y, scatter)
+
+
+def test_batch_plans_pick_the_spmm_kernels():
+    items = _setup(_mats(), KS)
+    kinds = [h.batch_spmm_kernel() for A, h, r, c, X in items]
+    assert kinds == ["rows" if i % 3 != 1 else "lanes" for i in range(len(items))]
+    for A, h, r, c, X in items:
+        h.close()
 
 
 def test_batch_item_alone_equals_in_mix_bitwise():
