@@ -1043,7 +1043,8 @@ def main():
                    "plain": round(2 * Z * world / (ms_plain * 1e-3) / 1e9, 2), "what": "2 nnz / time"},
         "permuted_over_plain": round(ms_plain / ms_perm, 4),
         "kernel_variant": {"permuted_items_per_lane": hP.items_per_lane(), "plain_items_per_lane": hN.items_per_lane(),
-                           "permuted_xslice": hP.xslice(), "plain_xslice": hN.xslice()},
+                           "permuted_xslice": hP.xslice(), "plain_xslice": hN.xslice(),
+                           "permuted_xslice_pairs": hP.xslice_pairs(), "permuted_stream_prefetch": hP.xslice_ahead()},
         "flushed_l2_launch_ms": {"permuted": fl_perm, "plain": fl_plain, "what": "median of 200 launches, "
                                  "a 256 MB write before each"},
         "seeds": seeds,

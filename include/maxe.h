@@ -221,7 +221,9 @@ MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, c
  * on pairs of CTAs (column halves), plus 0x1000 when SpMM takes one row per
  * group of lanes (MAXE_SPMM_ROWS), plus the SpMM kernel of the batch plan in
  * bits 13-14 (0 column passes, 1 columns across lanes, 2 one row per lane
- * group).  items: (host). */
+ * group), plus in bits 15-17 the x-sliced form's L2 prefetch distance along
+ * its entry stream in units of 512 entries (0: none; picked by MAXE_AUTOTUNE).
+ * items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;

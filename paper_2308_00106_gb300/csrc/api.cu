@@ -247,7 +247,7 @@ maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
   if (!h || !items) return MAXE_ERR_INVALID;
   *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0) | (h->xs_use ? 0x200 : 0) |
            (h->xs_use && h->xs_prefetch ? 0x400 : 0) | (h->xs_use && h->xs_pair == 2 ? 0x800 : 0) |
-           (h->spmm_rows ? 0x1000 : 0) | ((h->blc & 3) << 13);
+           (h->spmm_rows ? 0x1000 : 0) | ((h->blc & 3) << 13) | (((h->xs_ahead / 512) & 7) << 15);
   return MAXE_OK;
 }
 

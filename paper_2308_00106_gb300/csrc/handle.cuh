@@ -53,6 +53,8 @@ struct maxe_handle {
   int32_t xs_pair = 1;                     // column halves per tile: 1, or 2 on a cluster of two CTAs
   int32_t xs_smem = 0;                     // dynamic shared memory per CTA
   int64_t xs_bytes = 0;
+  int64_t xs_nent = 0;                     // entries allocated in xs_idx / xs_val (with the zeroed slack)
+  int32_t xs_ahead = 0;                    // L2 prefetch distance (entries) of the x-sliced stream, 0: none
   int xs_use = 0;                          // SpMV (k = 1) takes the x-sliced kernel
   int xs_prefetch = 0;                     // cells large enough for the L2 prefetch cursor
   int32_t* coo_row = nullptr;              // COO row index of every entry (MAXE_COO), else NULL

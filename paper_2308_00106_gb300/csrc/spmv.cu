@@ -238,9 +238,21 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st) {
   h->spmv_items16 = pick;
   // the x-sliced kernel, when the handle has it
   if (s == MAXE_OK && h->xs_idx) {
-    float ms = 0.f;
-    s = timed([&] { return xslice_launch(h, x, y, nullptr, st); }, &ms);
-    if (s == MAXE_OK) h->xs_use = ms < best ? 1 : 0;
+    // and its stream prefetch distance (entries; 0: none)
+    const int32_t dist[4] = {0, 512, 1024, 2048};
+    float best_xs = 1e30f;
+    int32_t pick_d = 0;
+    for (int d = 0; d < 4 && s == MAXE_OK; ++d) {
+      h->xs_ahead = dist[d];
+      float ms = 0.f;
+      s = timed([&] { return xslice_launch(h, x, y, nullptr, st); }, &ms);
+      if (s == MAXE_OK && ms < best_xs) {
+        best_xs = ms;
+        pick_d = dist[d];
+      }
+    }
+    h->xs_ahead = pick_d;
+    if (s == MAXE_OK) h->xs_use = best_xs < best ? 1 : 0;
   }
   // SpMM path for wide right-hand sides, timed at k = 16 when the scratch is modest
   const int64_t k = 16;

@@ -108,6 +108,8 @@ struct XsParams {
   const void* val;            // values, aligned with idx
   const int32_t* seg;         // [3 * cells]: first entry, steps S, layout word (see xs_layout)
   int64_t cells;
+  int64_t nent;               // entries allocated in idx and val
+  int32_t ahead;              // stream prefetch distance in entries (0: none; see xs_ahead)
   const int32_t* tile_row;    // [ntiles + 1]
   const int32_t* warp_row;    // [ntiles * J * (W + 1)] row ranges of the warps of each (tile, half)
   const int32_t* vslot;       // [ntiles * J * (W + 1)] virtual accumulators of the warps of each (tile, half)
@@ -362,6 +364,24 @@ __device__ __forceinline__ void xs_prefetch(const XsParams& p, const XsPos& q, i
               static_cast<uint32_t>((a1 - a0) * sizeof(ValT)));
 }
 
+// Without the cursor: a warp's cells for consecutive slices lie back to back
+// (cells are stored in (tile half, warp, slice) order), so its entries are one
+// contiguous stream; each group prefetches into L2 a group's worth of that
+// stream p.ahead entries past its own start, which can cover the DRAM latency
+// of the loads a few groups later at the cost of two bulk prefetches.  The
+// distance is the autotuner's pick per handle (0: off).
+
+template <typename ValT, int G>
+__device__ __forceinline__ void xs_ahead(const XsParams& p, const XsPos& q, int lane) {
+  if (q.i < 0 || lane != 0 || p.ahead == 0) return;
+  constexpr int64_t n = 32 * G;  // a multiple of 8 entries: 16-byte sizes in both arrays
+  const int64_t a0 = (static_cast<int64_t>(q.st) + 32 * q.s0 + p.ahead) & ~int64_t(7);
+  if (a0 + n > p.nent) return;
+  prefetch_l2(p.idx + a0, static_cast<uint32_t>(n * 4));
+  prefetch_l2(static_cast<const unsigned char*>(p.val) + a0 * static_cast<int64_t>(sizeof(ValT)),
+              static_cast<uint32_t>(n * sizeof(ValT)));
+}
+
 // acc[a] += value * x[column] for the lane's steps of the group, then the
 // warp synchronises (where two lanes' updates of one accumulator meet: the
 // builder keeps them in different groups).  FP64: steps that continue the
@@ -527,6 +547,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
       if (ok) xs_compute<VT, ValT, G>(kA, xb + ((v - 1) % NX) * SC, acc);
       qA = qn;
       if (qA.i >= 0) xs_load<ValT, G>(p, qA, lane, kA);
+      if constexpr (!PF) xs_ahead<ValT, G>(p, qA, lane);
       qn = xs_next<G>(p, g, qn, i1, lane, win);
       if constexpr (PF) {
         xs_prefetch<ValT, G>(p, qp, lane);
@@ -537,6 +558,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
       if (ok) xs_compute<VT, ValT, G>(kB, xb + ((v - 1) % NX) * SC, acc);
       qB = qn;
       if (qB.i >= 0) xs_load<ValT, G>(p, qB, lane, kB);
+      if constexpr (!PF) xs_ahead<ValT, G>(p, qB, lane);
       qn = xs_next<G>(p, g, qn, i1, lane, win);
       if constexpr (PF) {
         xs_prefetch<ValT, G>(p, qp, lane);
@@ -1018,6 +1040,8 @@ maxe_status xs_launch(const maxe_handle* h, const void* x, void* y, const int32_
   p.val = h->xs_val;
   p.seg = h->xs_seg;
   p.cells = h->xs_cells;
+  p.nent = h->xs_nent;
+  p.ahead = h->xs_ahead;
   p.tile_row = h->xs_tile_row;
   p.warp_row = h->xs_warp_row;
   p.vslot = h->xs_vslot;
@@ -1374,6 +1398,7 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool force_pair, 
   h->xs_pair = J;
   h->xs_smem = static_cast<int32_t>(xs_smem_bytes<VT, J>((maxslots + 31) & ~31));
   h->xs_bytes = Zp * (4 + vb) + 12 * cells;
+  h->xs_nent = Zp + kXsSlack;
   constexpr int64_t kPrefetchCell = 2 * 32 * XsCfg<VT, J>::kSteps;  // mean entries per cell from which the cursor runs
   h->xs_prefetch = nonempty > 0 && Z >= kPrefetchCell * nonempty ? 1 : 0;
   *built = 1;

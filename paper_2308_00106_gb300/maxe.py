@@ -258,6 +258,10 @@ class Handle:
         """True when SpMM takes one row per group of lanes (MAXE_SPMM_ROWS, or kept by the autotuner)."""
         return bool(self._tuning() & 0x1000)
 
+    def xslice_ahead(self) -> int:
+        """L2 prefetch distance (entries) of the x-sliced SpMV's entry stream (0: none)."""
+        return 512 * ((self._tuning() >> 15) & 7)
+
     def batch_spmm_kernel(self) -> str:
         """SpMM kernel of the handle's batch plan: "passes", "lanes" or "rows"."""
         return ("passes", "lanes", "rows", "passes")[(self._tuning() >> 13) & 3]
