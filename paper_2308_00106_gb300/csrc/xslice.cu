@@ -525,26 +525,32 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
         qp = xs_next<G>(p, g, qp, i1, lane, winp);
       }
     }
-    uint32_t v = 0;     // slices waited for
-    int i = i0;         // next slice to wait for
-    bool held = false;  // slice i - 1 is waited for and not yet released
+    int i = i0;          // next slice to wait for
+    int slot = 0;        // its ring slot
+    uint32_t par = 0;    // and the phase parity of that slot's barrier
+    int held = -1;       // slot of slice i - 1, waited for and not yet released (-1: none)
     bool ok = true;
-    auto advance_to = [&](int upto) {  // wait for slices up to `upto`, releasing the ones before
+    // Wait for slices up to `upto`, releasing the ones before.  A failed wait
+    // (the launch's limit ran out) stops the warp's waits and, through the
+    // flag, the producer's copies; the other warps' waits then run out too.
+    auto advance_to = [&](int upto) {
       while (i <= upto) {
-        if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
-        if (ok) {
-          ok = mbar_wait_bounded(&full[v % NX], (v / NX) & 1u, p.status, p.wait_ns);
-          ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
-          if (!ok) *abort_flag = 1;
+        if (held >= 0 && lane == 0 && ok) mbar_arrive(&empty[held]);
+        if (ok && !__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], par, p.status, p.wait_ns))) {
+          ok = false;
+          *abort_flag = 1;
         }
-        held = true;
+        held = slot;
+        if (++slot == NX) {
+          slot = 0;
+          par ^= 1u;
+        }
         ++i;
-        ++v;
       }
     };
     while (qA.i >= 0) {
       advance_to(qA.i);
-      if (ok) xs_compute<VT, ValT, G>(kA, xb + ((v - 1) % NX) * SC, acc);
+      if (ok) xs_compute<VT, ValT, G>(kA, xb + held * SC, acc);
       qA = qn;
       if (qA.i >= 0) xs_load<ValT, G>(p, qA, lane, kA);
       if constexpr (!PF) xs_ahead<ValT, G>(p, qA, lane);
@@ -555,7 +561,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
       }
       if (qB.i < 0) break;
       advance_to(qB.i);
-      if (ok) xs_compute<VT, ValT, G>(kB, xb + ((v - 1) % NX) * SC, acc);
+      if (ok) xs_compute<VT, ValT, G>(kB, xb + held * SC, acc);
       qB = qn;
       if (qB.i >= 0) xs_load<ValT, G>(p, qB, lane, kB);
       if constexpr (!PF) xs_ahead<ValT, G>(p, qB, lane);
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(kXsThreads, 1) spmv_xslice_kernel(const XsPara
       }
     }
     advance_to(i1 - 1);  // slices after this warp's last entries
-    if (held && lane == 0 && ok) mbar_arrive(&empty[(v - 1) % NX]);
+    if (held >= 0 && lane == 0 && ok) mbar_arrive(&empty[held]);
     __syncwarp();
     // virtual rows back into their rows, each split row by one lane, in order
     if (ok) {
