@@ -104,8 +104,9 @@ size_t xs_smem_bytes(int32_t slots) {
 }
 
 struct XsParams {
-  const uint32_t* idx;        // (accumulator << 15) | column in slice, cell by cell, step-major
-  const void* val;            // values, aligned with idx
+  const uint32_t* idx;        // (accumulator << 15) | column in slice, cell by cell, step-major; FP32
+                              // values: (index, value bits) pairs
+  const void* val;            // other values, aligned with idx (null for FP32)
   const int32_t* seg;         // [3 * cells]: first entry, steps S, layout word (see xs_layout)
   int64_t cells;
   int64_t nent;               // entries allocated in idx and val
@@ -302,6 +303,23 @@ __device__ __forceinline__ XsPos xs_next(const XsParams& p, int64_t g, const XsP
 // Load the lane's entries of the group's steps (layout: xs_layout).  Full
 // steps (nearly every cell) take one pointer per group and loads at constant
 // offsets; dealt cells take the general position.
+// FP32 values sit interleaved with their indices (one 8-byte entry); other
+// value types in an array of their own.
+template <typename ValT>
+constexpr bool kXsIlv = sizeof(ValT) == 4;
+
+// Bulk L2 prefetch of the n entries from a0 (multiples of 8: 16-byte bounds).
+template <typename ValT>
+__device__ __forceinline__ void xs_prefetch_entries(const XsParams& p, int64_t a0, int64_t n) {
+  if constexpr (kXsIlv<ValT>) {
+    prefetch_l2(p.idx + 2 * a0, static_cast<uint32_t>(n * 8));
+  } else {
+    prefetch_l2(p.idx + a0, static_cast<uint32_t>(n * 4));
+    prefetch_l2(static_cast<const unsigned char*>(p.val) + a0 * static_cast<int64_t>(sizeof(ValT)),
+                static_cast<uint32_t>(n * sizeof(ValT)));
+  }
+}
+
 template <typename ValT>
 __device__ __forceinline__ auto xs_val_ptr(const void* v) {
   if constexpr (sizeof(ValT) == 2)
@@ -318,13 +336,25 @@ __device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int l
     const int32_t ns = mine - q.s0;
     k.ns = ns < 0 ? 0 : (ns > G ? G : ns);
     const int64_t e0 = static_cast<int64_t>(q.st) + 32 * q.s0 + lane;
-    const uint32_t* pi = p.idx + e0;
-    const auto* pv = xs_val_ptr<ValT>(p.val) + e0;
+    if constexpr (kXsIlv<ValT>) {  // (index, value) in one 8-byte load
+      const uint2* pe = reinterpret_cast<const uint2*>(p.idx) + e0;
 #pragma unroll
-    for (int j = 0; j < G; ++j) {
-      if (j < k.ns) {
-        k.id[j] = __ldcs(pi + 32 * j);
-        k.set(j, static_cast<ValT>(__ldcs(pv + 32 * j)));
+      for (int j = 0; j < G; ++j) {
+        if (j < k.ns) {
+          const uint2 w = __ldcs(pe + 32 * j);
+          k.id[j] = w.x;
+          k.set(j, __uint_as_float(w.y));
+        }
+      }
+    } else {
+      const uint32_t* pi = p.idx + e0;
+      const auto* pv = xs_val_ptr<ValT>(p.val) + e0;
+#pragma unroll
+      for (int j = 0; j < G; ++j) {
+        if (j < k.ns) {
+          k.id[j] = __ldcs(pi + 32 * j);
+          k.set(j, static_cast<ValT>(__ldcs(pv + 32 * j)));
+        }
       }
     }
     return;
@@ -338,8 +368,14 @@ __device__ __forceinline__ void xs_load(const XsParams& p, const XsPos& q, int l
     if (j < k.ns) {
       const int32_t s = q.s0 + j;
       const int64_t pos = static_cast<int64_t>(q.st) + static_cast<int64_t>(s) * F + (s < P ? s : P) + lane;
-      k.id[j] = __ldcs(p.idx + pos);
-      k.set(j, XsVal<ValT>::raw(p.val, pos));
+      if constexpr (kXsIlv<ValT>) {
+        const uint2 w = __ldcs(reinterpret_cast<const uint2*>(p.idx) + pos);
+        k.id[j] = w.x;
+        k.set(j, __uint_as_float(w.y));
+      } else {
+        k.id[j] = __ldcs(p.idx + pos);
+        k.set(j, XsVal<ValT>::raw(p.val, pos));
+      }
     }
   }
 }
@@ -359,9 +395,7 @@ __device__ __forceinline__ void xs_prefetch(const XsParams& p, const XsPos& q, i
   const int64_t e0 = static_cast<int64_t>(q.st) + static_cast<int64_t>(q.s0) * F + (q.s0 < P ? q.s0 : P);
   const int64_t e1 = static_cast<int64_t>(q.st) + static_cast<int64_t>(s1) * F + (s1 < P ? s1 : P);
   const int64_t a0 = e0 & ~int64_t(7), a1 = (e1 + 7) & ~int64_t(7);  // 16-byte bounds of both arrays
-  prefetch_l2(p.idx + a0, static_cast<uint32_t>((a1 - a0) * 4));
-  prefetch_l2(static_cast<const unsigned char*>(p.val) + a0 * static_cast<int64_t>(sizeof(ValT)),
-              static_cast<uint32_t>((a1 - a0) * sizeof(ValT)));
+  xs_prefetch_entries<ValT>(p, a0, a1 - a0);
 }
 
 // Without the cursor: a warp's cells for consecutive slices lie back to back
@@ -377,9 +411,7 @@ __device__ __forceinline__ void xs_ahead(const XsParams& p, const XsPos& q, int 
   constexpr int64_t n = 32 * G;  // a multiple of 8 entries: 16-byte sizes in both arrays
   const int64_t a0 = (static_cast<int64_t>(q.st) + 32 * q.s0 + p.ahead) & ~int64_t(7);
   if (a0 + n > p.nent) return;
-  prefetch_l2(p.idx + a0, static_cast<uint32_t>(n * 4));
-  prefetch_l2(static_cast<const unsigned char*>(p.val) + a0 * static_cast<int64_t>(sizeof(ValT)),
-              static_cast<uint32_t>(n * sizeof(ValT)));
+  xs_prefetch_entries<ValT>(p, a0, n);
 }
 
 // acc[a] += value * x[column] for the lane's steps of the group, then the
@@ -957,7 +989,7 @@ __global__ void __launch_bounds__(32 * kXsOrderWarps) xs_order_kernel(
 // accumulator of its previous step inside the same register group of G steps
 // (kXsCont), so that the kernel keeps the running sum in a register there.
 __global__ void xs_cont_kernel(const int32_t* __restrict__ seg, const int32_t* __restrict__ counts, int64_t cells,
-                               int G, uint32_t* __restrict__ idx) {
+                               int G, int stride, uint32_t* __restrict__ idx) {
   const int64_t c = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= cells || counts[c] == 0) return;
@@ -966,13 +998,15 @@ __global__ void xs_cont_kernel(const int32_t* __restrict__ seg, const int32_t* _
   uint32_t prev = 0;
   for (int32_t s = 0; s < lay.mine; ++s) {
     const int64_t pos = static_cast<int64_t>(st) + static_cast<int64_t>(s) * lay.F + (s < lay.P ? s : lay.P) + lane;
-    const uint32_t v = idx[pos];
-    if (s % G != 0 && (v >> kXsColBits) == (prev >> kXsColBits)) idx[pos] = v | kXsCont;
+    const uint32_t v = idx[pos * stride];
+    if (s % G != 0 && (v >> kXsColBits) == (prev >> kXsColBits)) idx[pos * stride] = v | kXsCont;
     prev = v;
   }
 }
 
-// Sorted entry i goes to its slot: idx = (accumulator << 15) | column in slice.
+// Sorted entry i goes to its slot: idx = (accumulator << 15) | column in slice;
+// FP32 values interleaved with it (val_out null: entry pos is the 8 bytes
+// idx_out[2 pos], idx_out[2 pos + 1]), other types in their own array.
 __global__ void xs_scatter_kernel(const uint64_t* __restrict__ keys, const int32_t* __restrict__ vals, int64_t Z,
                                   const int32_t* __restrict__ outpos, const int32_t* __restrict__ col,
                                   const void* __restrict__ val, int vbytes, int32_t SC, int32_t nS,
@@ -985,7 +1019,13 @@ __global__ void xs_scatter_kernel(const uint64_t* __restrict__ keys, const int32
   const int32_t e = vals[i];
   const int64_t pos = outpos[i];
   const int32_t s = static_cast<int32_t>(cell % nS);
-  idx_out[pos] = (static_cast<uint32_t>(slot) << kXsColBits) | static_cast<uint32_t>(col[e] - s * SC);
+  const uint32_t id = (static_cast<uint32_t>(slot) << kXsColBits) | static_cast<uint32_t>(col[e] - s * SC);
+  if (!val_out) {
+    idx_out[2 * pos] = id;
+    idx_out[2 * pos + 1] = __float_as_uint(static_cast<const float*>(val)[e]);
+    return;
+  }
+  idx_out[pos] = id;
   if (vbytes == 8)
     static_cast<double*>(val_out)[pos] = static_cast<const double*>(val)[e];
   else if (vbytes == 4)
@@ -1358,14 +1398,15 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool force_pair, 
   const int64_t x_bytes = static_cast<int64_t>(tl_slice.size()) * sizeof(VT) * SC;
   if (!force && x_bytes > 8 * matrix_bytes) return MAXE_OK;  // the CSR kernel will do better
   if (Zp + kXsSlack > INT32_MAX) return MAXE_OK;
-  // ---- the format's arrays
-  uint32_t* idx = owned.get<uint32_t>(Zp + kXsSlack);
-  void* xval = owned.get<unsigned char>(static_cast<size_t>(vb) * (Zp + kXsSlack));
+  // ---- the format's arrays (FP32 values: one array of 8-byte (index, value) entries)
+  const bool ilv = h->dtype == MAXE_F32;
+  uint32_t* idx = owned.get<uint32_t>((ilv ? 2 : 1) * (Zp + kXsSlack));
+  void* xval = ilv ? nullptr : owned.get<unsigned char>(static_cast<size_t>(vb) * (Zp + kXsSlack));
   int32_t* d_seg = owned.get<int32_t>(3 * cells);
   int32_t* d_tl = owned.get<int32_t>(tl_off.size() + std::max<size_t>(tl_slice.size(), 1));
   int32_t* d_ustart = scratch.get<int32_t>(cells);
   int32_t* outpos = vals_alt;  // the sort's ping-pong values are free after it
-  if (!idx || !xval || !d_seg || !d_tl || !d_ustart) return MAXE_ERR_OOM;
+  if (!idx || (!ilv && !xval) || !d_seg || !d_tl || !d_ustart) return MAXE_ERR_OOM;
   MAXE_CUDA_TRY(cudaMemcpyAsync(d_seg, seg.data(), sizeof(int32_t) * 3 * cells, cudaMemcpyHostToDevice, st));
   MAXE_CUDA_TRY(cudaMemcpyAsync(d_ustart, ustart.data(), sizeof(int32_t) * cells, cudaMemcpyHostToDevice, st));
   MAXE_CUDA_TRY(cudaMemcpyAsync(d_tl, tl_off.data(), sizeof(int32_t) * tl_off.size(), cudaMemcpyHostToDevice, st));
@@ -1373,8 +1414,8 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool force_pair, 
     MAXE_CUDA_TRY(cudaMemcpyAsync(d_tl + tl_off.size(), tl_slice.data(), sizeof(int32_t) * tl_slice.size(),
                                   cudaMemcpyHostToDevice, st));
   // gaps between cells and the slack after the last one hold zeros
-  MAXE_CUDA_TRY(cudaMemsetAsync(idx, 0, sizeof(uint32_t) * (Zp + kXsSlack), st));
-  MAXE_CUDA_TRY(cudaMemsetAsync(xval, 0, static_cast<size_t>(vb) * (Zp + kXsSlack), st));
+  MAXE_CUDA_TRY(cudaMemsetAsync(idx, 0, sizeof(uint32_t) * (ilv ? 2 : 1) * (Zp + kXsSlack), st));
+  if (!ilv) MAXE_CUDA_TRY(cudaMemsetAsync(xval, 0, static_cast<size_t>(vb) * (Zp + kXsSlack), st));
   xs_pack_kernel<<<static_cast<unsigned>(ceil_div(cells, 128)), 128, 0, st>>>(keys, d_ustart, counts, mult, d_seg,
                                                                               cells, G, outpos);
   MAXE_CUDA_TRY(cudaGetLastError());
@@ -1384,7 +1425,8 @@ maxe_status build(maxe_handle* h, cudaStream_t st, bool force, bool force_pair, 
   xs_scatter_kernel<<<static_cast<unsigned>(ceil_div(Z, 256)), 256, 0, st>>>(keys, vals, Z, outpos, h->col, h->val,
                                                                              vb, SC, nS, idx, xval);
   MAXE_CUDA_TRY(cudaGetLastError());
-  xs_cont_kernel<<<static_cast<unsigned>(ceil_div(cells * 32, 256)), 256, 0, st>>>(d_seg, counts, cells, G, idx);
+  xs_cont_kernel<<<static_cast<unsigned>(ceil_div(cells * 32, 256)), 256, 0, st>>>(d_seg, counts, cells, G,
+                                                                                   ilv ? 2 : 1, idx);
   MAXE_CUDA_TRY(cudaGetLastError());
   MAXE_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors and scratch go out of scope
   owned.keep();
