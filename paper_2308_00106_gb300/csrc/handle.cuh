@@ -38,8 +38,9 @@ struct maxe_handle {
   int blc = 0;                             // batch plan, SpMM: 0 column passes, 1 columns across lanes, 2 rows
   int bbps = 0;                            // batch plan: CTAs per SM of its launch (0: as many as fit)
   // x-sliced SpMV form (MAXE_XSLICE): entries grouped by ((tile, half, warp range), column slice)
-  uint32_t* xs_idx = nullptr;              // (accumulator << 15) | column in slice, step-major cells
-  void* xs_val = nullptr;
+  uint32_t* xs_idx = nullptr;              // (accumulator << 15) | column in slice, step-major cells;
+                                           // with FP32 values (index, value bits) pairs
+  void* xs_val = nullptr;                  // BF16 / FP64 values beside xs_idx (null for FP32)
   int32_t* xs_seg = nullptr;               // [3 * cells]: first entry, steps, full lanes | partial entries << 6
   int64_t xs_cells = 0;
   int32_t* xs_tile_row = nullptr;          // [ntiles + 1]
