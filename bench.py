@@ -618,8 +618,9 @@ def serving_measure(seed, requests, loads=(0.5, 0.8, 0.95), unbatched=True):
     out = {
         "value": round(sat["gbs"], 3), "unit": "GB/s",
         "config": {"workload": "64 square matrices, rows log-uniform 10k-4M, Poisson(U[5,50]) row lengths, half "
-                               "FP32 half BF16 values, R-C permuted; requests 60% SpMV, 30% SpMM k~U{2..32}, 10% "
-                               "20-step power iteration; device-memory admission cap 60 GB",
+                               "FP32 half BF16 values, R-C permuted, autotuned handles (x-sliced SpMV where faster); "
+                               "requests 60% SpMV, 30% SpMM k~U{2..32}, 10% 20-step power iteration; device-memory "
+                               "admission cap 60 GB",
                    "requests_per_trace": n, "resident_bytes": srv.resident_bytes,
                    "total_nnz": int(sum(A.nnz for A in mats))},
         "saturation": sat, "loads": at,

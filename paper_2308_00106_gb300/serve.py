@@ -89,7 +89,8 @@ class Server:
     """Resident permuted matrices + the continuous-batching loop."""
 
     def __init__(self, mats, seed: int = 2308, mem_cap_bytes: int = 60 << 30, streams: int = 2,
-                 tune: bool = False, batch_capacity: int = 4096, step_bytes: int = 2 << 30):
+                 tune: bool = False, batch_capacity: int = 4096, step_bytes: int = 2 << 30,
+                 autotune: bool = True):
         maxe.load(build_if_missing=True)
         self.mats = mats
         self.handles, self.Q, self.perm_c = [], [], []
@@ -97,7 +98,9 @@ class Server:
         for m, A in enumerate(mats):
             r = maxe.maxe_build_permutation(seed + m, A.rows, 0)
             c = maxe.maxe_build_permutation(seed + m, A.cols, 1)
-            h = maxe.from_csr(A, r, c)
+            # autotuned handles: the x-sliced SpMV where it is faster, and the
+            # fastest SpMM kernel (which the handle's batch plan then takes)
+            h = maxe.from_csr(A, r, c, autotune=autotune)
             if tune:
                 maxe.maxe_batch_tune(h, 1)
             self.handles.append(h)
@@ -157,17 +160,27 @@ class Server:
                 r.bufs = {"X": X[:, :r.k], "Y": torch.empty(A.rows, kp, device="cuda")[:, :r.k]}
 
     def _launch(self, si: int, reqs):
+        """One step on stream si: the products of `reqs` (single SpMV launches
+        where the handle runs the x-sliced form, which one persistent batched
+        launch would not use; one batched launch per kernel class for the
+        rest), then the power iterations' vector steps."""
         s = self.streams[si]
-        items = []
+        items, singles = [], []
         for r in reqs:
             h = self.handles[r.mat]
             if r.kind == "power":
-                items.append((h, r.bufs["u"], r.bufs["w"], False))
+                x, y = r.bufs["u"], r.bufs["w"]
             else:
-                items.append((h, r.bufs["X"], r.bufs["Y"], False))
+                x, y = r.bufs["X"], r.bufs["Y"]
+            if (r.kind == "power" or r.k == 1) and h.xslice():
+                singles.append((h, x.reshape(-1), y.reshape(-1)))
+            else:
+                items.append((h, x, y, False))
         b = self.batches[si]
         b.set(items)
         b.run(stream=s)
+        for h, x, y in singles:
+            maxe.maxe_spmv(h, x, y, permuted=True, stream=s)
         with torch.cuda.stream(s):
             for r in reqs:
                 if r.kind != "power":
