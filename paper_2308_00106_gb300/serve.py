@@ -90,7 +90,7 @@ class Server:
 
     def __init__(self, mats, seed: int = 2308, mem_cap_bytes: int = 60 << 30, streams: int = 2,
                  tune: bool = False, batch_capacity: int = 4096, step_bytes: int = 2 << 30,
-                 autotune: bool = True):
+                 autotune: bool = True, xslice: bool = False):
         maxe.load(build_if_missing=True)
         self.mats = mats
         self.handles, self.Q, self.perm_c = [], [], []
@@ -99,8 +99,9 @@ class Server:
             r = maxe.maxe_build_permutation(seed + m, A.rows, 0)
             c = maxe.maxe_build_permutation(seed + m, A.cols, 1)
             # autotuned handles: the x-sliced SpMV where it is faster, and the
-            # fastest SpMM kernel (which the handle's batch plan then takes)
-            h = maxe.from_csr(A, r, c, autotune=autotune)
+            # fastest SpMM kernel (which the handle's batch plan then takes);
+            # xslice: the x-sliced form on every handle
+            h = maxe.from_csr(A, r, c, autotune=autotune and not xslice, xslice=xslice)
             if tune:
                 maxe.maxe_batch_tune(h, 1)
             self.handles.append(h)

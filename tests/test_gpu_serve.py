@@ -15,17 +15,37 @@ from tests.gpu_common import code, rel_l2
 pytestmark = pytest.mark.gpu
 
 
+def _mats():
+    return [W.poisson_uniform(500 + m, rows, lam, "f32" if m % 2 == 0 else "bf16", device="cuda")
+            for m, (rows, lam) in enumerate([(2000, 5.0), (9000, 20.0), (30000, 12.0), (4000, 45.0),
+                                             (60000, 8.0), (15000, 30.0)])]
+
+
 @pytest.fixture(scope="module")
 def server():
     maxe.load(build_if_missing=True)
-    mats = [W.poisson_uniform(500 + m, rows, lam, "f32" if m % 2 == 0 else "bf16", device="cuda")
-            for m, (rows, lam) in enumerate([(2000, 5.0), (9000, 20.0), (30000, 12.0), (4000, 45.0),
-                                             (60000, 8.0), (15000, 30.0)])]
-    srv = serve.Server(mats, seed=77, mem_cap_bytes=8 << 30)
+    srv = serve.Server(_mats(), seed=77, mem_cap_bytes=8 << 30)
     yield srv
     srv.close()
     torch.cuda.synchronize()
     assert maxe.maxe_device_status() == maxe.MAXE_OK
+
+
+@pytest.fixture(scope="module")
+def server_xs():
+    """Every handle with the x-sliced form: SpMV products go out as single x-sliced launches."""
+    maxe.load(build_if_missing=True)
+    srv = serve.Server(_mats(), seed=77, mem_cap_bytes=8 << 30, xslice=True)
+    assert all(h.xslice() for h in srv.handles)
+    yield srv
+    srv.close()
+    torch.cuda.synchronize()
+    assert maxe.maxe_device_status() == maxe.MAXE_OK
+
+
+@pytest.fixture(params=["autotuned", "xsliced"])
+def any_server(request, server, server_xs):
+    return server if request.param == "autotuned" else server_xs
 
 
 def _check(srv, r):
@@ -49,7 +69,8 @@ def _check(srv, r):
         assert rel_l2(r.result.cpu().numpy(), ref) <= 1e-5
 
 
-def test_serving_results_match_oracle(server):
+def test_serving_results_match_oracle(any_server):
+    server = any_server
     trace = serve.make_trace(40, len(server.mats), math.inf, seed=3, mix=(0.4, 0.4, 0.2), kmax=8, steps=6)
     stats = server.run(trace, keep_results=True)
     assert stats["requests"] == 40 and stats["max_batch"] > 1
@@ -57,7 +78,8 @@ def test_serving_results_match_oracle(server):
         _check(server, r)
 
 
-def test_serving_same_alone_and_in_mix(server):
+def test_serving_same_alone_and_in_mix(any_server):
+    server = any_server
     trace = serve.make_trace(30, len(server.mats), 4000.0, seed=9, mix=(0.4, 0.4, 0.2), kmax=8, steps=5)
     server.run(trace, keep_results=True)
     for r in trace:
