@@ -707,7 +707,8 @@ def run_laplacian_table(args):
                 rows_out.append({"dtype": dtype, "order": order, "k": k, "ms": round(ms, 4), "gbs": round(gbs, 1),
                                  "frac": round(gbs / hbm, 4), "gflops": round(2 * A.nnz * k / (ms * 1e-3) / 1e9, 1),
                                  "items_per_lane": h.items_per_lane(), "xslice": bool(k == 1 and h.xslice()),
-                                 "spmm_path": None if k == 1 else ("rows" if h.spmm_rows() else
+                                 "spmm_path": None if k == 1 else (("rows+pf" if h.spmm_rows_prefetch() else "rows")
+                                                                   if h.spmm_rows() else
                                                                    "lanes" if h.spmm_lanes() else "passes"),
                                  "build_s": round(t_build, 4)})
             h.close()

@@ -115,6 +115,11 @@ typedef enum { MAXE_F64 = 0, MAXE_F32 = 1, MAXE_BF16 = 2 } maxe_dtype;
  * of 4 (FP32 vectors) / 2 (FP64) (tuning override; MAXE_AUTOTUNE times it
  * against the other SpMM paths at k = 16 and keeps the fastest). */
 #define MAXE_SPMM_ROWS 0x400u
+/* Flag of maxe_permute_csr: with MAXE_SPMM_ROWS, each lane group also
+ * prefetches into L2 the X rows of its next row while it sums the current one
+ * (tuning override; MAXE_AUTOTUNE times the rows kernel with and without it).
+ * Results do not depend on it. */
+#define MAXE_SPMM_ROWS_PF 0x800u
 
 /* Device memory allocator used for everything a handle owns and for scratch.
  * alloc(bytes, ctx, stream) returns a device pointer aligned to >= 256 bytes or
@@ -222,8 +227,11 @@ MAXE_API maxe_status maxe_handle_csr(const maxe_handle* h, maxe_csr* view_out, c
  * group of lanes (MAXE_SPMM_ROWS), plus the SpMM kernel of the batch plan in
  * bits 13-14 (0 column passes, 1 columns across lanes, 2 one row per lane
  * group), plus in bits 15-17 the x-sliced form's L2 prefetch distance along
- * its entry stream in units of 512 entries (0: none; picked by MAXE_AUTOTUNE).
- * items: (host). */
+ * its entry stream in units of 512 entries (0: none; picked by MAXE_AUTOTUNE),
+ * plus 0x40000 when the one-row-per-lane-group SpMM prefetches each lane
+ * group's next X rows into L2 (picked by MAXE_AUTOTUNE: it pays where
+ * neighbouring rows share X rows, as in a stencil, and costs on permuted
+ * matrices).  items: (host). */
 MAXE_API maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items);
 
 /* a4.  Entropy of the nonzero distribution (Section 4, entropy equation;

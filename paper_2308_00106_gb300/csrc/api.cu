@@ -184,7 +184,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (A->nnz > 0 && (A->rows == 0 || A->cols == 0)) return MAXE_ERR_INVALID;
   if (flags & ~static_cast<uint32_t>(MAXE_VALIDATE | MAXE_AUTOTUNE | MAXE_ITEMS16 | MAXE_SPMM_LANES |
                                      MAXE_EQUAL_ROWS | MAXE_COO | MAXE_XSLICE | MAXE_XS_PAIRS | MAXE_XS_SINGLE |
-                                     MAXE_SPMM_ROWS))
+                                     MAXE_SPMM_ROWS | MAXE_SPMM_ROWS_PF))
     return MAXE_ERR_INVALID;
   if ((flags & MAXE_XS_PAIRS) && (flags & MAXE_XS_SINGLE)) return MAXE_ERR_INVALID;
   DeviceInfo di{};
@@ -217,6 +217,7 @@ maxe_status maxe_permute_csr(const maxe_csr* A, const int32_t* rperm, const int3
   if (s == MAXE_OK && (flags & MAXE_ITEMS16)) h->spmv_items16 = 1;
   if (s == MAXE_OK && (flags & MAXE_SPMM_LANES)) h->spmm_lc = 1;
   if (s == MAXE_OK && (flags & MAXE_SPMM_ROWS)) h->spmm_rows = 1;
+  if (s == MAXE_OK && (flags & MAXE_SPMM_ROWS_PF)) h->spmm_rows_pf = 1;
   if (s == MAXE_OK && (flags & MAXE_AUTOTUNE)) s = spmv_autotune(h, st);
   // the default batch plan follows the handle's SpMM path where it was tuned
   // or asked for, else takes the rows kernel
@@ -247,7 +248,8 @@ maxe_status maxe_handle_tuning(const maxe_handle* h, int32_t* items) {
   if (!h || !items) return MAXE_ERR_INVALID;
   *items = (h->spmv_items16 ? 16 : 8) | (h->spmm_lc ? 0x100 : 0) | (h->xs_use ? 0x200 : 0) |
            (h->xs_use && h->xs_prefetch ? 0x400 : 0) | (h->xs_use && h->xs_pair == 2 ? 0x800 : 0) |
-           (h->spmm_rows ? 0x1000 : 0) | ((h->blc & 3) << 13) | (((h->xs_ahead / 512) & 7) << 15);
+           (h->spmm_rows ? 0x1000 : 0) | ((h->blc & 3) << 13) | (((h->xs_ahead / 512) & 7) << 15) |
+           (h->spmm_rows_pf ? 0x40000 : 0);
   return MAXE_OK;
 }
 

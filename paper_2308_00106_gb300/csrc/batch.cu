@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) spmm_batch_rows_kernel(BatchParams b
       if (bp.task0[mid] <= t) lo = mid; else hi = mid - 1;
     }
     const BatchItem& it = bp.items[lo];
-    const rows::RowsOperand op{it.rowptr, it.col, it.val, it.X, it.Y, it.yperm, it.ldx, it.ldy, it.k};
+    const rows::RowsOperand op{it.rowptr, it.col, it.val, it.X, it.Y, it.yperm, it.ldx, it.ldy, it.k, 0};
     const int w = t - bp.task0[lo];
     rows::rows_range<VT>(s, op, it.wrow[w], it.wrow[w + 1], rows::rows_group<VT>(it.k), lane);
     int nt = 0;

@@ -30,6 +30,7 @@ struct maxe_handle {
   int spmv_items16 = 0;                    // chosen SpMV variant (autotuned or 0)
   int spmm_lc = 0;                         // SpMM with columns across lanes (autotuned or 0)
   int spmm_rows = 0;                       // SpMM with one row per lane group (autotuned or 0)
+  int spmm_rows_pf = 0;                    // that kernel prefetches each group's next X rows (autotuned)
   int equal_rows = 0;                      // SpMV partition: equal rows per warp (not equal nonzeros)
   int32_t* bwrow = nullptr;                // batch plan: partition with bH entries per warp task
   int32_t bnW = 0;

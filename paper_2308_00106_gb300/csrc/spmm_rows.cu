@@ -173,6 +173,7 @@ maxe_status spmm_rows_launch(const maxe_handle* h, int32_t k, const void* X, int
   p.op.ldx = ldx;
   p.op.ldy = ldy;
   p.op.k = k;
+  p.op.pf = h->spmm_rows_pf;
   p.wrow = h->wrow[0];
   p.nW = h->nW[0];
   // parts of about kPartE entries: a warp's range cut into Q parts of equal row counts

@@ -123,6 +123,7 @@ struct RowsOperand {
   const int32_t* yperm;  // Y row of row r: yperm[r] (null: r)
   int64_t ldx, ldy;
   int32_t k;
+  int32_t pf;  // 1: prefetch the X rows of a group's next row into L2 (stencil-like matrices)
 };
 
 // Row pointers rowptr[r + j], j = 0 .. min(kChunkR, b - r): j = lane in *pa,
@@ -194,6 +195,14 @@ __device__ __forceinline__ void rows_chunk(const RowsStage<VT>* s, int buf, cons
     const int32_t t0 = s->rp[buf][j], t1 = s->rp[buf][j + 1];
     const int64_t yr = p.yperm ? static_cast<int64_t>(__ldg(p.yperm + r0 + j)) : static_cast<int64_t>(r0 + j);
     const int32_t ts = min(t1, lim);  // staged entries of the row end here
+    // the X rows of the group's next row into L2, one line each (when a row
+    // spans several lanes: with one lane per row the prefetches cost more)
+    if (p.pf && G > 1 && j + GPW < n) {
+      const int32_t u0 = s->rp[buf][j + GPW], u1 = min(s->rp[buf][j + GPW + 1], lim);
+      for (int32_t u = u0 + sub; u < u1 && u < u0 + kRowsUnroll * G; u += G)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const char*>(p.X) +
+                                                       static_cast<int64_t>(scol[u]) * static_cast<int64_t>(ldx_bytes)));
+    }
     for (int c = sub; c < kv; c += G) {
       // X piece c of row COL: xc + COL * ldx_bytes (one wide multiply-add per entry)
       const char* xc = static_cast<const char*>(p.X) + 16 * c;

@@ -266,8 +266,15 @@ maxe_status spmv_autotune(maxe_handle* h, cudaStream_t st) {
       if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 0); }, &t_pass);
       if (s == MAXE_OK) s = timed([&] { return spmm_launch(h, k, X, k, Y, k, nullptr, st, -1, 1); }, &t_lc);
       const bool rows_ok = spmm_rows_ready(h, static_cast<int32_t>(k), X, k, Y, k);
-      if (s == MAXE_OK && rows_ok)
+      if (s == MAXE_OK && rows_ok) {  // with and without its next-row prefetch
+        float t_pf = 0.f;
+        h->spmm_rows_pf = 0;
         s = timed([&] { return spmm_rows_launch(h, k, X, k, Y, k, nullptr, st); }, &t_rows);
+        h->spmm_rows_pf = 1;
+        if (s == MAXE_OK) s = timed([&] { return spmm_rows_launch(h, k, X, k, Y, k, nullptr, st); }, &t_pf);
+        h->spmm_rows_pf = t_pf < t_rows ? 1 : 0;
+        t_rows = std::min(t_rows, t_pf);
+      }
       if (s == MAXE_OK) {
         h->spmm_lc = t_lc < t_pass ? 1 : 0;
         h->spmm_rows = rows_ok && t_rows < std::min(t_pass, t_lc) ? 1 : 0;

@@ -34,6 +34,7 @@ MAXE_XSLICE = 0x80
 MAXE_XS_PAIRS = 0x100
 MAXE_XS_SINGLE = 0x200
 MAXE_SPMM_ROWS = 0x400
+MAXE_SPMM_ROWS_PF = 0x800
 
 DTYPE_CODE = {"f64": MAXE_F64, "f32": MAXE_F32, "bf16": MAXE_BF16}
 VAL_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.bfloat16}
@@ -258,6 +259,10 @@ class Handle:
         """True when SpMM takes one row per group of lanes (MAXE_SPMM_ROWS, or kept by the autotuner)."""
         return bool(self._tuning() & 0x1000)
 
+    def spmm_rows_prefetch(self) -> bool:
+        """True when the rows SpMM kernel prefetches each lane group's next X rows (autotuned)."""
+        return bool(self._tuning() & 0x40000)
+
     def xslice_ahead(self) -> int:
         """L2 prefetch distance (entries) of the x-sliced SpMV's entry stream (0: none)."""
         return 512 * ((self._tuning() >> 15) & 7)
@@ -330,7 +335,7 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
                      rperm: torch.Tensor | None = None, cperm: torch.Tensor | None = None, validate: bool = False,
                      stream=None, autotune: bool = False, items16: bool = False, spmm_lanes: bool = False,
                      equal_rows: bool = False, coo: bool = False, xslice: bool = False,
-                     xs_pairs: bool | None = None, spmm_rows: bool = False) -> Handle:
+                     xs_pairs: bool | None = None, spmm_rows: bool = False, spmm_rows_pf: bool = False) -> Handle:
     """Handle of A' = P_r A P_c (Eq. 1) with ascending columns; None perms = identity.
     xs_pairs: None lets the library decide whether the x-sliced form runs its
     tiles on CTA pairs (column halves); True / False forces it on / off."""
@@ -349,7 +354,7 @@ def maxe_permute_csr(rows: int, cols: int, rowptr: torch.Tensor, col: torch.Tens
              | (MAXE_SPMM_LANES if spmm_lanes else 0) | (MAXE_EQUAL_ROWS if equal_rows else 0)
              | (MAXE_COO if coo else 0) | (MAXE_XSLICE if xslice else 0)
              | (0 if xs_pairs is None else (MAXE_XS_PAIRS if xs_pairs else MAXE_XS_SINGLE))
-             | (MAXE_SPMM_ROWS if spmm_rows else 0))
+             | (MAXE_SPMM_ROWS if spmm_rows else 0) | (MAXE_SPMM_ROWS_PF if spmm_rows_pf else 0))
     _check(load().maxe_permute_csr(ctypes.byref(A), _ptr(rperm), _ptr(cperm), flags,
                                    ctypes.byref(_ALLOC), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
            "maxe_permute_csr")
@@ -443,10 +448,11 @@ def maxe_version() -> str:
 
 
 def from_csr(A, rperm=None, cperm=None, validate=False, stream=None, autotune=False, items16=False,
-             spmm_lanes=False, equal_rows=False, coo=False, xslice=False, xs_pairs=None, spmm_rows=False) -> Handle:
+             spmm_lanes=False, equal_rows=False, coo=False, xslice=False, xs_pairs=None, spmm_rows=False,
+             spmm_rows_pf=False) -> Handle:
     """Handle from a workloads.CSR already on the GPU."""
     return maxe_permute_csr(A.rows, A.cols, A.rowptr, A.col, A.val, rperm, cperm, validate, stream, autotune, items16,
-                            spmm_lanes, equal_rows, coo, xslice, xs_pairs, spmm_rows)
+                            spmm_lanes, equal_rows, coo, xslice, xs_pairs, spmm_rows, spmm_rows_pf)
 
 
 class Batch:

@@ -160,12 +160,14 @@ def test_spmv_laplacian_closed_form_ones():
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 16, 33, 64])
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("lanes", ["passes", "lanes", "rows"])
+@pytest.mark.parametrize("lanes", ["passes", "lanes", "rows", "rows_pf"])
 def test_spmm_against_oracle(k, dtype, lanes):
     A = edge_matrix("ragged", dtype, seed=k)
     rperm, cperm = _perms(A, k, "rc")
-    h = maxe.from_csr(A.to("cuda"), rperm, cperm, spmm_lanes=lanes == "lanes", spmm_rows=lanes == "rows")
-    assert h.spmm_lanes() == (lanes == "lanes") and h.spmm_rows() == (lanes == "rows")
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, spmm_lanes=lanes == "lanes", spmm_rows=lanes.startswith("rows"),
+                      spmm_rows_pf=lanes == "rows_pf")
+    assert h.spmm_lanes() == (lanes == "lanes") and h.spmm_rows() == lanes.startswith("rows")
+    assert h.spmm_rows_prefetch() == (lanes == "rows_pf")
     X = W.matrix_rhs(k, A.cols, k, "f64" if dtype == "f64" else "f32", "cuda")
     rp, co, va = A.numpy()
     Yo = oracle.spmm(A.rows, rp, co, va, code(dtype), X.cpu().numpy())
@@ -192,14 +194,15 @@ def test_spmm_against_oracle(k, dtype, lanes):
 
 
 @pytest.mark.parametrize("kind", ["long_rows", "empty_runs", "unit_rows"])
-@pytest.mark.parametrize("lanes", ["passes", "lanes", "rows"])
+@pytest.mark.parametrize("lanes", ["passes", "lanes", "rows", "rows_pf"])
 def test_spmm_columns_match_spmv(kind, lanes):
     """Every column of an SpMM, and the SpMV of that column, are each within the
     FP32 bound of the FP64 oracle (the two kernels sum in different orders;
     rows here reach 70,000 entries)."""
     A = edge_matrix(kind, "f32", seed=2)
     rperm, cperm = _perms(A, 3, "rc")
-    h = maxe.from_csr(A.to("cuda"), rperm, cperm, spmm_lanes=lanes == "lanes", spmm_rows=lanes == "rows")
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, spmm_lanes=lanes == "lanes", spmm_rows=lanes.startswith("rows"),
+                      spmm_rows_pf=lanes == "rows_pf")
     X = W.matrix_rhs(4, A.cols, 12, "f32", "cuda")
     Y = maxe.maxe_spmm(h, X)
     rp, co, va = A.numpy()
