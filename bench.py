@@ -656,6 +656,38 @@ def run_serving(args):
         print(json.dumps(out))
 
 
+def run_spmm_profile(args):
+    """SpMM with the rows kernel on a natural-order 5-point Laplacian (grid x
+    grid, FP32, k columns): 3 products then 20 timed ones, for ncu captures of
+    spmm_rows_kernel (`-s 3 -c 1` takes the first timed launch)."""
+    from paper_2308_00106_gb300 import maxe
+    from paper_2308_00106_gb300 import workloads as W
+
+    maxe.load(build_if_missing=True)
+    A = W.laplacian5(args.grid, "f32", "cuda")
+    h = maxe.from_csr(A, spmm_rows=True, spmm_rows_pf=args.rows_pf)
+    k = args.k
+    X = W.matrix_rhs(1, A.cols, k, "f32", "cuda")
+    Y = torch.empty(A.rows, k, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        maxe.maxe_spmm(h, X, Y, permuted=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        maxe.maxe_spmm(h, X, Y, permuted=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 20
+    by = alg_bytes(A.rows, A.cols, A.nnz, 4, 4, 4, k)
+    hbm, src = peaks()
+    print(json.dumps({"workload": f"5-point Laplacian {args.grid}^2 natural, FP32, k = {k}, rows kernel"
+                                  + (" with next-row prefetch" if args.rows_pf else ""),
+                      "ms": round(ms, 4), "gbs": round(by / (ms * 1e-3) / 1e9, 1),
+                      "frac": round(by / (ms * 1e-3) / 1e9 / hbm, 4), "alg_bytes": by, "peak_source": src}))
+    h.close()
+
+
 def run_laplacian_table(args):
     """5-point Laplacian, n = 4096 (16.8M rows, 83.9M nonzeros): FP64 / FP32 /
     BF16 values x natural / permuted order x SpMM k = 1, 4, 16."""
@@ -871,9 +903,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["maxe", "reference"], default="maxe")
     ap.add_argument("--workload", choices=["powerlaw", "laplacian", "blockdiag", "clustered", "batched", "serving",
-                                           "laplacian-table", "partition-table", "shuffle-table"],
+                                           "laplacian-table", "partition-table", "shuffle-table", "spmm-profile"],
                     default="powerlaw")
     ap.add_argument("--requests", type=int, default=1500, help="requests per serving trace")
+    ap.add_argument("--grid", type=int, default=2048, help="spmm-profile: Laplacian grid side")
+    ap.add_argument("--k", type=int, default=16, help="spmm-profile: right-hand sides")
+    ap.add_argument("--rows-pf", action="store_true", help="spmm-profile: rows kernel with its next-row prefetch")
     ap.add_argument("--batch-count", type=int, default=256, help="matrices of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: default batch plans, no autotuning")
     ap.add_argument("--items-per-lane", choices=["auto", "8", "16"], default="auto",
@@ -911,6 +946,8 @@ def main():
         return run_shuffle_table(args)
     if args.workload == "partition-table":
         return run_partition_table(args)
+    if args.workload == "spmm-profile":
+        return run_spmm_profile(args)
     if args.workload == "laplacian-table":
         return run_laplacian_table(args)
 
