@@ -291,10 +291,11 @@ def seed_sweep(A, x, args, world, tune):
             "what": "seeds 0..n-1 for the row and column permutations; 200 products each (CUDA graph)"}
 
 
-def timed_streams(step, streams, K, W, world):
+def timed_streams(step, streams, K, W, world, host_ms=None):
     """W warm-up steps, then exactly K steps step(k) that spread over `streams`;
     device time from an event before the first to one after all streams drain
-    (barrier + synchronize on both sides); ms per step, max over ranks."""
+    (barrier + synchronize on both sides); ms per step, max over ranks.  With a
+    list host_ms, appends the host's time per step to enqueue the K steps."""
     for k in range(W):
         step(k)
     torch.cuda.synchronize()
@@ -305,8 +306,11 @@ def timed_streams(step, streams, K, W, world):
     e0.record(cur)
     for st in streams:
         st.wait_event(e0)
+    t0 = time.perf_counter()
     for k in range(K):
         step(k)
+    if host_ms is not None:
+        host_ms.append((time.perf_counter() - t0) * 1e3 / K)
     for st in streams:
         cur.wait_stream(st)
     e1.record(cur)
@@ -911,6 +915,8 @@ def main():
     ap.add_argument("--rows-pf", action="store_true", help="spmm-profile: rows kernel with its next-row prefetch")
     ap.add_argument("--batch-count", type=int, default=256, help="matrices of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched workload: default batch plans, no autotuning")
+    ap.add_argument("--e2e-streams", type=int, default=3,
+                    help="streams the end-to-end steps rotate over (each with its own host and device buffers)")
     ap.add_argument("--items-per-lane", choices=["auto", "8", "16"], default="auto",
                     help="SpMV kernel variant: autotuned per handle, or fixed")
     ap.add_argument("--xslice", action="store_true",
@@ -931,6 +937,8 @@ def main():
     ap.add_argument("--record-profile", nargs=4, metavar=("CSV", "KERNEL", "LAUNCH", "COMMAND"),
                     help="write profiles/<record>.json from an ncu raw CSV export (no GPU needed)")
     args = ap.parse_args()
+    if args.e2e_streams < 1:
+        ap.error("--e2e-streams must be at least 1")
     if args.record_profile:
         csv_path, kernel, launch, command = args.record_profile
         print(json.dumps(record_profile(csv_path, kernel, int(launch), command, args.workload)))
@@ -1021,25 +1029,26 @@ def main():
 
     nrp, ncol, nval, _, _ = hP.csr()
 
-    # ---- end to end through the public API with host buffers: every step copies
-    # its x' from pinned host memory, runs the product and copies y' back; steps
-    # alternate between two streams with their own buffers, so one step's
-    # copies overlap another's product
+    # ---- end to end through the public API with host buffers: every step is one
+    # maxe_spmv_host call that copies its x' from pinned host memory, runs the
+    # product and copies y' back; steps rotate over --e2e-streams streams with
+    # their own buffers, so one step's copies overlap the other steps' products
+    # (with two, a stream's D2H of one step and H2D of its next step must both
+    # fit in the time of one product)
     K_e2e = max(args.steps // 4, 2)
-    e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    e2e_streams = [torch.cuda.Stream() for _ in range(args.e2e_streams)]
     e2e_bufs = [(xp.cpu().pin_memory(), torch.empty_like(xp), torch.empty(M, dtype=vdt, device="cuda"),
                  torch.empty(M, dtype=vdt).pin_memory()) for _ in e2e_streams]
 
     def step_e2e(k):
-        st = e2e_streams[k % 2]
-        xh, xd, yd, yh = e2e_bufs[k % 2]
-        with torch.cuda.stream(st):
-            xd.copy_(xh, non_blocking=True)
-            maxe.maxe_spmv(hP, xd, yd, permuted=True, stream=st)
-            yh.copy_(yd, non_blocking=True)
+        st = e2e_streams[k % len(e2e_streams)]
+        xh, xd, yd, yh = e2e_bufs[k % len(e2e_streams)]
+        maxe.maxe_spmv_host(hP, xh, yh, xd, yd, permuted=True, stream=st)
 
-    ms_e2e = timed_streams(step_e2e, e2e_streams, K_e2e, args.warmup, world)
-    np.testing.assert_array_equal(e2e_bufs[0][3].numpy(), e2e_bufs[1][3].numpy())  # same product on both streams
+    host_e2e = []
+    ms_e2e = timed_streams(step_e2e, e2e_streams, K_e2e, args.warmup, world, host_e2e)
+    for b in e2e_bufs[1:]:
+        np.testing.assert_array_equal(e2e_bufs[0][3].numpy(), b[3].numpy())  # same product on every stream
     if not torch.equal(e2e_bufs[0][3].cuda(), yP):
         raise SystemExit("end-to-end result differs from the timed device result")
 
@@ -1098,8 +1107,9 @@ def main():
                      "bytes_per_launch": bytes_step, "kernel": kern},
         "e2e": {"value": round(job_rate(bytes_step, ms_e2e, world) / 1e9, 3), "unit": "GB/s",
                 "h2d_bytes_per_step": N * xb, "d2h_bytes_per_step": M * xb, "ms_per_step": ms_e2e,
-                "what": "per step: H2D of x' from pinned memory, y' = A' x' (maxe_spmv), D2H of y'; "
-                        "steps alternate over two streams"},
+                "host_enqueue_ms_per_step": round(host_e2e[0], 5),
+                "what": "per step: one maxe_spmv_host call (H2D of x' from pinned memory, y' = A' x', D2H of y'); "
+                        f"steps rotate over {args.e2e_streams} streams"},
         "gpu_launches": args.steps,
         "clocks": clk,
         **({"by_dtype": by_dtype} if by_dtype else {}),

@@ -287,6 +287,21 @@ MAXE_API maxe_status maxe_nnz_entropy_noalloc(const maxe_handle* h, int32_t gr, 
  * without MAXE_VEC_PERMUTED share its x' scratch: do not overlap them in time. */
 MAXE_API maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uint32_t flags, void* stream);
 
+/* a6 + a5 from host memory (Section 2, CSR product): enqueues on `stream`, in
+ * this order, the copy of x_host into x_dev, maxe_spmv(h, x_dev, y_dev, flags,
+ * stream) and the copy of y_dev into y_host, and returns without waiting:
+ * y_host holds y once `stream` has passed the call (synchronise the stream or
+ * wait on an event recorded after it).  x_host: (host) cols elements, y_host:
+ * (host) rows elements, element type as for maxe_spmv; page-locked host memory
+ * lets the copies run asynchronously, while from pageable memory the CUDA
+ * driver stages them and the call may block.  x_dev, y_dev: (device) scratch
+ * of cols / rows elements owned by the caller, not overlapping each other or
+ * the host buffers' device mappings; x_dev is overwritten.  Flags and the x'
+ * scratch as for maxe_spmv.  Errors: INVALID on NULL pointers or unknown flags
+ * (nothing enqueued); CUDA when a copy cannot be enqueued. */
+MAXE_API maxe_status maxe_spmv_host(const maxe_handle* h, const void* x_host, void* y_host, void* x_dev, void* y_dev,
+                                    uint32_t flags, void* stream);
+
 /* f3.  y = A x over the COO form of the handle (Section 2, COO product): the
  * row-sorted triplets of A' in chunks of 256 entries, one warp per chunk,
  * rows that cross chunk edges finished by a second kernel from per-chunk

@@ -275,6 +275,20 @@ maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uint32_t fla
   return spmm_launch(h, 1, xs, 1, y, 1, h->rperm, st);
 }
 
+maxe_status maxe_spmv_host(const maxe_handle* h, const void* x_host, void* y_host, void* x_dev, void* y_dev,
+                           uint32_t flags, void* stream) {
+  if (!h || flags & ~static_cast<uint32_t>(MAXE_VEC_PERMUTED)) return MAXE_ERR_INVALID;
+  if ((h->cols > 0 && (!x_host || !x_dev)) || (h->rows > 0 && (!y_host || !y_dev))) return MAXE_ERR_INVALID;
+  cudaStream_t st = as_stream(stream);
+  const size_t eb = vector_bytes(h->dtype);
+  if (h->cols > 0)
+    MAXE_CUDA_TRY(cudaMemcpyAsync(x_dev, x_host, eb * static_cast<size_t>(h->cols), cudaMemcpyHostToDevice, st));
+  MAXE_TRY(maxe_spmv(h, x_dev, y_dev, flags, stream));
+  if (h->rows > 0)
+    MAXE_CUDA_TRY(cudaMemcpyAsync(y_host, y_dev, eb * static_cast<size_t>(h->rows), cudaMemcpyDeviceToHost, st));
+  return MAXE_OK;
+}
+
 maxe_status maxe_coo_spmv(const maxe_handle* h, const void* x, void* y, uint32_t flags, void* stream) {
   if (!h || flags & ~static_cast<uint32_t>(MAXE_VEC_PERMUTED)) return MAXE_ERR_INVALID;
   if ((h->cols > 0 && !x) || (h->rows > 0 && !y)) return MAXE_ERR_INVALID;

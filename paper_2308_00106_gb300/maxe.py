@@ -42,7 +42,7 @@ VEC_TORCH = {MAXE_F64: torch.float64, MAXE_F32: torch.float32, MAXE_BF16: torch.
 
 EXPORTS = [
     "maxe_build_permutation", "maxe_invert_permutation", "maxe_permute_gather", "maxe_permute_scatter",
-    "maxe_permute_csr", "maxe_handle_csr", "maxe_handle_tuning", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmm", "maxe_power_iteration",
+    "maxe_permute_csr", "maxe_handle_csr", "maxe_handle_tuning", "maxe_nnz_entropy", "maxe_spmv", "maxe_spmv_host", "maxe_spmm", "maxe_power_iteration",
     "maxe_handle_destroy", "maxe_device_status", "maxe_status_str", "maxe_version",
     "maxe_batch_create", "maxe_batch_set", "maxe_batch_run", "maxe_batch_destroy", "maxe_batch_tune",
     "maxe_batch_plan_info", "maxe_vec_norm_gather", "maxe_vec_dot_gather", "maxe_entropy_levels",
@@ -125,6 +125,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             "maxe_handle_tuning": [P, ctypes.POINTER(I32)],
             "maxe_nnz_entropy": [P, I32, I32, ctypes.c_double, ctypes.POINTER(ctypes.c_double), P, P, P],
             "maxe_spmv": [P, P, P, U32, P],
+            "maxe_spmv_host": [P, P, P, P, P, U32, P],
             "maxe_spmm": [P, I32, P, I64, P, I64, U32, P],
             "maxe_power_iteration": [P, P, I32, P, ctypes.POINTER(ctypes.c_double), P],
             "maxe_power_iteration_history": [P, P, I32, P, ctypes.POINTER(ctypes.c_double),
@@ -381,6 +382,34 @@ def maxe_spmv(h: Handle, x: torch.Tensor, y: torch.Tensor | None = None, permute
     _check(load().maxe_spmv(ctypes.c_void_p(h.ptr), _ptr(x), _ptr(y), MAXE_VEC_PERMUTED if permuted else 0,
                             ctypes.c_void_p(_stream(stream))), "maxe_spmv")
     return y
+
+
+def _host(t: torch.Tensor, dtype, n: int, name: str) -> torch.Tensor:
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return t
+
+
+def maxe_spmv_host(h: Handle, x_host: torch.Tensor, y_host: torch.Tensor, x_dev: torch.Tensor, y_dev: torch.Tensor,
+                   permuted: bool = False, stream=None):
+    """y = A x from host memory in one library call: x_host is copied into the
+    device scratch x_dev, the product written to y_dev and copied into y_host,
+    all enqueued on `stream`; y_host holds y once the stream has passed the
+    call.  Pinned host tensors let the copies run asynchronously."""
+    _host(x_host, h.vec_dtype, h.cols, "x_host")
+    _host(y_host, h.vec_dtype, h.rows, "y_host")
+    _dev(x_dev, h.vec_dtype, "x_dev")
+    _dev(y_dev, h.vec_dtype, "y_dev")
+    if x_dev.numel() != h.cols or y_dev.numel() != h.rows:
+        raise ValueError("x_dev / y_dev have the wrong length")
+    _check(load().maxe_spmv_host(ctypes.c_void_p(h.ptr), _ptr(x_host), _ptr(y_host), _ptr(x_dev), _ptr(y_dev),
+                                 MAXE_VEC_PERMUTED if permuted else 0, ctypes.c_void_p(_stream(stream))),
+           "maxe_spmv_host")
+    return y_host
 
 
 def maxe_coo_spmv(h: Handle, x: torch.Tensor, y: torch.Tensor | None = None, permuted: bool = False, stream=None):

@@ -11,6 +11,7 @@
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <cuda_runtime.h>
 
@@ -95,6 +96,14 @@ int main(int argc, char** argv) {
 
   maxe_status refused = maxe_spmv(h, d_x, d_y, 0x80000000u, NULL);
 
+  /* the same product from host memory in one call (pageable buffers) */
+  double* y2 = (double*)malloc(sizeof(double) * (size_t)n);
+  double* d_x2 = NULL;
+  if (!y2) return 2;
+  CHECK_CUDA(cudaMalloc((void**)&d_x2, sizeof(double) * (size_t)n));
+  CHECK_MAXE(maxe_spmv_host(h, x, y2, d_x2, d_y, 0u, NULL));
+  CHECK_CUDA(cudaDeviceSynchronize());
+
   int bad = 0;
   for (int32_t i = 0; i < n; ++i) {
     double want = i == 0 ? -1.0 : (i == n - 1 ? (double)n : 0.0);
@@ -103,13 +112,19 @@ int main(int argc, char** argv) {
       ++bad;
     }
   }
+  for (int32_t i = 0; i < n; ++i) {
+    if (memcmp(&y2[i], &y[i], sizeof(double)) != 0) {
+      if (bad < 5) fprintf(stderr, "host-buffer y[%d] = %.17g, device call %.17g\n", i, y2[i], y[i]);
+      ++bad;
+    }
+  }
   if (H != 0.0) { fprintf(stderr, "1x1 entropy %.17g, want 0\n", H); ++bad; }
   if (refused != MAXE_ERR_INVALID) { fprintf(stderr, "unknown flag: %s\n", maxe_status_str(refused)); ++bad; }
 
   CHECK_MAXE(maxe_handle_destroy(h));
   cudaFree(d_rowptr); cudaFree(d_col); cudaFree(d_val); cudaFree(d_rperm); cudaFree(d_cperm);
-  cudaFree(d_x); cudaFree(d_y);
-  free(rowptr); free(col); free(val); free(x); free(y);
+  cudaFree(d_x); cudaFree(d_y); cudaFree(d_x2);
+  free(rowptr); free(col); free(val); free(x); free(y); free(y2);
   printf("maxe %s: n=%d seed=%llu, %d wrong\n", maxe_version(), n, (unsigned long long)seed, bad);
   return bad ? 1 : 0;
 }

@@ -62,6 +62,9 @@ def test_host_checks_reject_bad_arguments_without_launching(lib_path):
     assert lib.maxe_build_permutation(1, 0, 0, None, None, None) == 0
     lib.maxe_spmv.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_uint32, ctypes.c_void_p]
     assert lib.maxe_spmv(None, None, None, 0, None) == 1
+    lib.maxe_spmv_host.argtypes = [ctypes.c_void_p] * 5 + [ctypes.c_uint32, ctypes.c_void_p]
+    assert lib.maxe_spmv_host(None, None, None, None, None, 0, None) == 1
+    assert lib.maxe_spmv_host(None, None, None, None, None, 0x80, None) == 1
     lib.maxe_handle_destroy.argtypes = [ctypes.c_void_p]
     assert lib.maxe_handle_destroy(None) == 0
 

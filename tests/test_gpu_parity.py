@@ -132,6 +132,51 @@ def test_spmv_edges_original_and_permuted_space(kind, dtype, items16):
         np.testing.assert_array_equal(yp.cpu().numpy()[torch.argsort(rperm).cpu().numpy()], y.cpu().numpy())
 
 
+@pytest.mark.parametrize("case", ["ragged", "empty_nnz", "rect_wide", "rect_tall", "laplacian_xslice"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_spmv_host_buffers_equal_the_device_call(case, dtype, pinned):
+    """maxe_spmv_host (copy in, product, copy out, one stream) gives the bits of
+    maxe_spmv on device vectors in both spaces, and the oracle's product."""
+    A = W.laplacian5(300, dtype) if case == "laplacian_xslice" else edge_matrix(case, dtype, seed=7)
+    rperm, cperm = _perms(A, 5, "rc")
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, xslice=case == "laplacian_xslice")
+    vt = torch.float64 if dtype == "f64" else torch.float32
+    x = W.vector(9, A.cols, "f64" if dtype == "f64" else "f32", "cuda")
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    got = {}
+    for permuted in (False, True):
+        xh = x.cpu()
+        yh = torch.full((A.rows,), float("nan"), dtype=vt)
+        if pinned:
+            xh, yh = xh.pin_memory(), yh.pin_memory()
+        xd = torch.full_like(x, float("nan"))
+        yd = torch.empty(A.rows, dtype=vt, device="cuda")
+        assert maxe.maxe_spmv_host(h, xh, yh, xd, yd, permuted=permuted, stream=st) is yh
+        st.synchronize()
+        ref = maxe.maxe_spmv(h, x, permuted=permuted)
+        np.testing.assert_array_equal(yh.numpy(), ref.cpu().numpy())
+        got[permuted] = yh.numpy().copy()
+    rp, co, va = A.numpy()
+    assert rel_l2(got[False], oracle.spmv(A.rows, rp, co, va, code(dtype), x.cpu().numpy())) <= TOL[dtype]
+    nrp, nco, nva = oracle_permuted(A, rperm, cperm)
+    assert rel_l2(got[True], oracle.spmv(A.rows, nrp, nco, nva, code(dtype), x.cpu().numpy())) <= TOL[dtype]
+
+
+def test_spmv_host_rejects_device_tensors_and_wrong_lengths():
+    A = edge_matrix("ragged", "f32", seed=7)
+    h = maxe.from_csr(A.to("cuda"))
+    xd = torch.zeros(A.cols, device="cuda")
+    yd = torch.zeros(A.rows, device="cuda")
+    with pytest.raises(ValueError):
+        maxe.maxe_spmv_host(h, xd, yd.cpu(), xd, yd)
+    with pytest.raises(ValueError):
+        maxe.maxe_spmv_host(h, xd.cpu()[:-1], yd.cpu(), xd, yd)
+    with pytest.raises(TypeError):
+        maxe.maxe_spmv_host(h, xd.cpu().double(), yd.cpu(), xd, yd)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("mode", ["plain", "rc"])
 def test_spmv_laplacian_and_blockdiag(dtype, mode):
