@@ -1109,7 +1109,9 @@ def main():
                 "h2d_bytes_per_step": N * xb, "d2h_bytes_per_step": M * xb, "ms_per_step": ms_e2e,
                 "host_enqueue_ms_per_step": round(host_e2e[0], 5),
                 "what": "per step: one maxe_spmv_host call (H2D of x' from pinned memory, y' = A' x', D2H of y'); "
-                        f"steps rotate over {args.e2e_streams} streams"},
+                        f"steps rotate over {args.e2e_streams} streams",
+                "note": "products on different streams overlap one kernel's last CTAs with the next one's first, "
+                        "so this can match or pass `value`, which replays the products on one stream"},
         "gpu_launches": args.steps,
         "clocks": clk,
         **({"by_dtype": by_dtype} if by_dtype else {}),
