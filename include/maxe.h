@@ -295,9 +295,8 @@ MAXE_API maxe_status maxe_spmv(const maxe_handle* h, const void* x, void* y, uin
  * (host) rows elements, element type as for maxe_spmv; page-locked host memory
  * lets the copies run asynchronously, while from pageable memory the CUDA
  * driver stages them and the call may block.  x_dev, y_dev: (device) scratch
- * of cols / rows elements owned by the caller, not overlapping each other or
- * the host buffers' device mappings; x_dev is overwritten.  Flags and the x'
- * scratch as for maxe_spmv.  Errors: INVALID on NULL pointers or unknown flags
+ * of cols / rows elements owned by the caller, not overlapping each other;
+ * x_dev is overwritten.  Flags and the x' scratch as for maxe_spmv.  Errors: INVALID on NULL pointers or unknown flags
  * (nothing enqueued); CUDA when a copy cannot be enqueued. */
 MAXE_API maxe_status maxe_spmv_host(const maxe_handle* h, const void* x_host, void* y_host, void* x_dev, void* y_dev,
                                     uint32_t flags, void* stream);
