@@ -396,6 +396,14 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
     MAXE_CUDA_TRY(cudaEventSynchronize(b->uploaded));
     b->pending = false;
   }
+  // items without nonzeros: Y = 0, written here; no kernel reads their X
+  for (const maxe_batch_item& a : b->items) {
+    const maxe_handle* h = a.h;
+    if (h->rows == 0 || h->nnz > 0) continue;
+    const size_t eb = static_cast<size_t>(vector_bytes(h->dtype));
+    MAXE_CUDA_TRY(cudaMemset2DAsync(a.Y, static_cast<size_t>(a.ldy) * eb, 0, static_cast<size_t>(a.k) * eb,
+                                    static_cast<size_t>(h->rows), st));
+  }
   const maxe_dtype types[3] = {MAXE_F64, MAXE_F32, MAXE_BF16};
   for (int g = 0; g < 3 * kClasses; ++g) {
     const int ti = g / kClasses, cls = g % kClasses;
@@ -407,7 +415,7 @@ maxe_status maxe_batch_run(maxe_batch* b, void* stream) {
     bool any_default = false;
     for (const maxe_batch_item& a : b->items) {
       const maxe_handle* h = a.h;
-      if (h->dtype != types[ti] || h->rows == 0) continue;
+      if (h->dtype != types[ti] || h->rows == 0 || h->nnz == 0) continue;
       const int eb = vector_bytes(h->dtype);
       const int vw = pick_vw(a, eb);
       const int unit = (a.k == 1 && a.ldx == 1 && a.ldy == 1) ? 1 : 0;

@@ -149,6 +149,12 @@ maxe_status spmv_build_partition(maxe_handle* h, cudaStream_t st) {
 maxe_status spmm_launch(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y, int64_t ldy,
                         const int32_t* yperm, cudaStream_t st, int variant, int lc) {
   if (h->rows == 0 || k == 0) return MAXE_OK;
+  if (h->nnz == 0) {  // Y = 0 whatever X holds; X is not read (with no columns it holds nothing)
+    const size_t eb = static_cast<size_t>(vector_bytes(h->dtype));
+    MAXE_CUDA_TRY(cudaMemset2DAsync(Y, static_cast<size_t>(ldy) * eb, 0, static_cast<size_t>(k) * eb,
+                                    static_cast<size_t>(h->rows), st));
+    return MAXE_OK;
+  }
   Params p{};
   p.rowptr = h->rowptr;
   p.col = h->col;

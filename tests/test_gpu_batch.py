@@ -183,6 +183,36 @@ def test_batch_run_in_cuda_graph():
         assert torch.equal(y, r_)
 
 
+def test_batch_items_without_nonzeros_are_zero():
+    """Items with no nonzeros -- no columns at all, or an empty pattern -- come
+    out as zeros without any kernel reading their X (which holds no element
+    when there are no columns); the other items keep the bits they have alone."""
+    mats = [edge_matrix("ragged", "f32", seed=5), W.from_lengths(1, [0] * 7, 0, "f32"),
+            W.from_lengths(1, [0] * 9, 13, "f64")]
+    ks = [3, 2, 5]
+    g = torch.Generator().manual_seed(11)
+    items, Ys = [], []
+    for A, k in zip(mats, ks):
+        vt = torch.float64 if A.dtype == "f64" else torch.float32
+        ld = (k + 3) // 4 * 4
+        X = torch.rand(A.cols, ld, generator=g, dtype=torch.float64).to(vt).cuda()[:, :k]
+        Y = torch.full((A.rows, ld), float("nan"), dtype=vt, device="cuda")[:, :k]
+        items.append((maxe.from_csr(A.to("cuda")), X))
+        Ys.append(Y)
+    b = maxe.Batch(len(items))
+    b.set([(h, X, Y, False) for (h, X), Y in zip(items, Ys)])
+    b.run()
+    h, X = items[0]
+    Yalone = torch.full((mats[0].rows, 4), float("nan"), device="cuda")[:, :3]
+    b1 = maxe.Batch(1)
+    b1.set([(h, X, Yalone, False)])
+    b1.run()
+    torch.cuda.synchronize()
+    assert torch.equal(Ys[0], Yalone)
+    assert torch.equal(Ys[1], torch.zeros_like(Ys[1]))
+    assert torch.equal(Ys[2], torch.zeros_like(Ys[2]))
+
+
 def test_batch_rejects_bad_items():
     A = edge_matrix("ragged", "f32")
     h = maxe.from_csr(A.to("cuda"))

@@ -164,6 +164,36 @@ def test_spmv_host_buffers_equal_the_device_call(case, dtype, pinned):
     assert rel_l2(got[True], oracle.spmv(A.rows, nrp, nco, nva, code(dtype), x.cpu().numpy())) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("shape", [(0, 5), (5, 0), (0, 0)])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_zero_row_and_zero_column_matrices(shape, dtype):
+    """Degenerate shapes (no rows or no columns, so no nonzeros): every product
+    is an empty or an all-zero vector, in both spaces and through every entry
+    point; x holds no element when there are no columns and is never read."""
+    M, N = shape
+    A = W.from_lengths(1, [0] * M, N, dtype)
+    rperm, cperm = _perms(A, 3, "rc")
+    h = maxe.from_csr(A.to("cuda"), rperm, cperm, coo=True)
+    vt = torch.float64 if dtype == "f64" else torch.float32
+    x = torch.zeros(N, dtype=vt, device="cuda")
+    for permuted in (False, True):
+        y = torch.full((M,), float("nan"), dtype=vt, device="cuda")
+        maxe.maxe_spmv(h, x, y, permuted=permuted)
+        assert torch.equal(y, torch.zeros_like(y))
+        y = torch.full((M,), float("nan"), dtype=vt, device="cuda")
+        maxe.maxe_coo_spmv(h, x, y, permuted=permuted)
+        assert torch.equal(y, torch.zeros_like(y))
+        for k in (3, 16):
+            Y = torch.full((M, k), float("nan"), dtype=vt, device="cuda")
+            maxe.maxe_spmm(h, torch.zeros(N, k, dtype=vt, device="cuda"), Y, permuted=permuted)
+            assert torch.equal(Y, torch.zeros_like(Y))
+        yh = torch.full((M,), float("nan"), dtype=vt)
+        maxe.maxe_spmv_host(h, x.cpu(), yh, torch.empty(N, dtype=vt, device="cuda"),
+                            torch.empty(M, dtype=vt, device="cuda"), permuted=permuted)
+        torch.cuda.synchronize()
+        assert torch.equal(yh, torch.zeros_like(yh))
+
+
 def test_spmv_host_rejects_device_tensors_and_wrong_lengths():
     A = edge_matrix("ragged", "f32", seed=7)
     h = maxe.from_csr(A.to("cuda"))
