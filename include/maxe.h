@@ -320,7 +320,9 @@ MAXE_API maxe_status maxe_handle_coo(const maxe_handle* h, const int32_t** row);
  * MAXE_VEC_PERMUTED, rows of X are gathered into handle-owned scratch.
  * Speed: with 16-byte aligned X and Y and ldx, ldy multiples of 4 (FP32) or 2
  * (FP64), rows are gathered 4 (2) columns per load, also when k is not a
- * multiple (the padding columns of X are read and ignored; Y's are untouched). */
+ * multiple (the padding columns of X are read and ignored; Y's are untouched).
+ * A handle without nonzeros writes Y = 0 without reading X, which may then be
+ * NULL when cols == 0 (the same holds for maxe_spmv's x and y). */
 MAXE_API maxe_status maxe_spmm(const maxe_handle* h, int32_t k, const void* X, int64_t ldx, void* Y,
                       int64_t ldy, uint32_t flags, void* stream);
 
@@ -365,7 +367,9 @@ typedef struct {
 MAXE_API maxe_status maxe_batch_create(int32_t capacity, const maxe_allocator* alloc, void* stream, maxe_batch** out);
 /* Replace the item list (host array of n items, copied).  INVALID on bad items. */
 MAXE_API maxe_status maxe_batch_set(maxe_batch* b, const maxe_batch_item* items, int32_t n);
-/* Upload the table and launch the persistent kernel(s) on `stream`. */
+/* Upload the table and launch the persistent kernel(s) on `stream`; the Y of
+ * items whose handle has no nonzeros is zeroed by a memset instead (their X is
+ * not read). */
 MAXE_API maxe_status maxe_batch_run(maxe_batch* b, void* stream);
 MAXE_API maxe_status maxe_batch_destroy(maxe_batch* b);
 /* Autotune the handle's batch plan for k right-hand sides.  Two batches of
