@@ -59,3 +59,11 @@ def test_headline_kernel_record_matches_its_sources():
         "xslice.cu or internal.cuh changed since the ncu record was taken: capture and record it again"
     alg = bench.alg_bytes(1 << 20, 1 << 20, 25394653, 4, 4, 4)
     assert 0.9 * alg < rec["traffic_bytes_per_launch"] < 3 * alg
+
+
+def test_bench_rejects_an_empty_e2e_stream_rotation():
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--e2e-streams", "0"],
+                       capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert r.returncode == 2
+    assert "--e2e-streams must be at least 1" in r.stderr
